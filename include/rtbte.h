@@ -1,0 +1,242 @@
+/*
+ * rtbte.h -- C ABI of the GB300 (sm_103a) library for the coupled electron/phonon
+ * real-time Boltzmann equation (rt-BTE) of arXiv 2412.13402.
+ *
+ * The library evaluates the right-hand side of Eq. bte,
+ *     df_{nk}/dt  = I^{e-ph}[f, N]                    (Eq. e-ph, first integral)
+ *     dN_{nu q}/dt = I^{ph-e}[f, N] + I^{ph-ph}[N]     (Eq. e-ph second integral, Eq. ph-ph)
+ * on the state vector y = [f_{nk}; N_{nu q}] (Eq. state_vec), and advances it with the
+ * integrators of Methods B: fixed-step RK4, adaptive explicit RK with an embedded error
+ * estimate (Eq. ERK_method), the WRMS norm (Eqs. wrms_norm, wrms_weights), the PID step
+ * controller (Eq. pid_controller), and the explicit MRI/MIS method (Eq. mis_coef) with the
+ * fast/slow split of Eq. mri_rhs.  The scattering channels are "computed and stored before
+ * the real-time simulation" (Results, rt-BTE section); rtbte_upload_channels builds or
+ * copies them.
+ *
+ * Conventions
+ *   - Units: energies in eV (phonon tables hold hbar*omega), time in ps, hbar in eV*ps.
+ *   - Every call returns RTBTE_OK (0) or a negative RTBTE_E_* code; rtbte_last_error()
+ *     gives a one-line message.  No call traps the device or aborts the process.
+ *   - Host arrays passed in descriptors are read during the call only (the library keeps
+ *     its own copies).  Device arrays (y, ydot) are owned by the caller.
+ *   - All GPU work is ordered on the context's stream; the calls return when their work
+ *     is enqueued, except where stated (rtbte_advance_to and host-pointer rtbte_rhs
+ *     synchronise the stream before returning).
+ *   - One context serves one device; it is not thread-safe (one host thread at a time).
+ */
+#ifndef RTBTE_H
+#define RTBTE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTBTE_VERSION 1
+
+/* ---- status codes ------------------------------------------------------- */
+#define RTBTE_OK 0
+#define RTBTE_E_INVALID_ARG (-1)    /* bad pointer, size or option                       */
+#define RTBTE_E_OOM (-2)            /* device or host allocation failed                  */
+#define RTBTE_E_CUDA (-3)           /* a CUDA runtime call failed                        */
+#define RTBTE_E_TOO_MANY_STEPS (-4) /* max_steps reached before t_out                    */
+#define RTBTE_E_STEP_UNDERFLOW (-5) /* step size fell below hmin                         */
+#define RTBTE_E_ERR_TEST_FAIL (-6)  /* max_nef consecutive error-test failures           */
+#define RTBTE_E_NONFINITE (-7)      /* NaN/Inf in a stage, the solution or the norm      */
+#define RTBTE_E_TIMEOUT (-8)        /* a bounded device wait gave up                     */
+#define RTBTE_E_STATE (-9)          /* call out of order (e.g. rhs before channels)      */
+#define RTBTE_E_UNSUPPORTED (-10)   /* sizes beyond the packed-index formats             */
+
+/* ---- right-hand-side parts (Eq. erk_rhs / Eq. mri_rhs) ------------------- */
+#define RTBTE_EPH 1u  /* I^{e-ph}: electron rows                                        */
+#define RTBTE_PHE 2u  /* I^{ph-e}: phonon rows fed by e-ph absorption                   */
+#define RTBTE_PHPH 4u /* I^{ph-ph}: phonon rows, three-phonon processes                 */
+#define RTBTE_FAST (RTBTE_EPH | RTBTE_PHE)
+#define RTBTE_SLOW RTBTE_PHPH
+#define RTBTE_ALL (RTBTE_EPH | RTBTE_PHE | RTBTE_PHPH)
+
+/* ---- arithmetic of the collision sums ------------------------------------ */
+#define RTBTE_PREC_FP32_COMP 0 /* FP32 gathers/products, compensated FP32 sums, FP64 out */
+#define RTBTE_PREC_FP64 1      /* FP64 weights, populations, products and sums          */
+
+/* One simulation instance: grids, bands, phonon branches, couplings (Methods A).
+ * Electron state s (0..n_c-1) is the s-th kept (band, k) pair in the order the caller
+ * lists them; e_k gives its integer grid coordinates on the nk grid.  Phonon state
+ * p = nu*N_q + q_lin with q_lin = (qz*nq[1] + qy)*nq[0] + qx.  The phonon wave vector of
+ * the e-ph term linking k (destination) to k' (source) is q = T(k' - k): the minimum-image
+ * difference on the electron grid (each component in (-nk/2, nk/2]) divided by `fold`
+ * with truncation, modulo nq.  ph-ph acts on the phonons whose q coordinates are all
+ * multiples of pp_stride (pp_stride = 0: no ph-ph).  Coupling strengths are
+ * |g|^2 = g2_coef[nu] * lut[i] and |V3|^2 = v3_coef * lut[i], where i is the top lut_bits
+ * bits of h = mix64(key ^ mix64(seed)), mix64 being SplitMix64's output function
+ * (z += 0x9E3779B97F4A7C15; z = (z^(z>>30))*0xBF58476D1CE4E5B9; z = (z^(z>>27))*0x94D049BB133111EB;
+ * z^(z>>31)).  e-ph key: with u = band*N_k + k_lin for the two electron states and v their
+ * images under k -> -k, take the sorted pairs (lo,hi) of u and of v, keep the
+ * lexicographically smaller, key = (lo*U + hi)*nmodes + nu, U = nbands*N_k.  ph-ph key:
+ * the full phonon indices of the three participants sorted, likewise for their q -> -q
+ * images, the smaller triple (t1,t2,t3) gives key = (t1*N_ph + t2)*N_ph + t3.  Both keys,
+ * and hence the couplings, are symmetric under exchange of the participants and inversion. */
+typedef struct rtbte_instance_desc {
+    int32_t dim;       /* 2 or 3                                                   */
+    int32_t fold;      /* nk[c] / nq[c] for every used dimension (1 or 2)          */
+    int32_t nbands;    /* electron bands                                            */
+    int32_t nmodes;    /* phonon branches                                           */
+    int32_t nk[3];     /* electron grid (nk[2] = 1 in 2D)                          */
+    int32_t nq[3];     /* phonon grid                                               */
+    int32_t n_c;       /* kept electron states                                      */
+    int32_t pp_stride; /* ph-ph sub-lattice stride (0: no ph-ph)                    */
+    int32_t lut_bits;  /* log2 of the coupling look-up table length (1..20)        */
+    int32_t reserved0;
+    const int32_t *e_band;   /* host [n_c]                                          */
+    const int32_t *e_k;      /* host [n_c*3] grid coordinates                        */
+    const double *e_eps;     /* host [n_c] band energies, eV                          */
+    const double *ph_omega;  /* host [nmodes*N_q] hbar*omega, eV                     */
+    const double *lut;       /* host [2^lut_bits] lognormal shape factors            */
+    const double *g2_coef;   /* host [nmodes] |g|^2 medians, eV^2                    */
+    double v3_coef;          /* |V3|^2 median                                        */
+    double sigma_eph;        /* Gaussian broadening of I^{e-ph}, I^{ph-e}, eV        */
+    double sigma_pp;         /* Gaussian broadening of I^{ph-ph}, eV                 */
+    double omega_cut;        /* phonons with hbar*omega below this are frozen, eV     */
+    uint64_t g2_seed, v3_seed;
+} rtbte_instance_desc;
+
+typedef struct rtbte_desc {
+    int32_t n_instances;  /* independent simulations sharing one state vector        */
+    int32_t precision;    /* RTBTE_PREC_*                                           */
+    const rtbte_instance_desc *inst; /* host [n_instances]                           */
+    double hbar;          /* eV*ps                                                   */
+    void *stream;         /* cudaStream_t used for every launch (NULL: default stream) */
+    int32_t device;       /* CUDA device ordinal (must be current for every call)    */
+    int32_t reserved1;
+} rtbte_desc;
+
+/* Channel source for rtbte_upload_channels.
+ * mode RTBTE_CH_BUILD: the device builder enumerates the channels from the instance
+ *   tables (all other fields ignored).
+ * mode RTBTE_CH_PREBUILT: host CSR arrays in the library's logical order (no padding):
+ *   e-ph  segments g = (nu*n_c + d)*2 + proc (proc 0 emission, 1 absorption), entries
+ *         (src electron, full phonon p) sorted by src, weight (2 pi/hbar)(1/N_q)|g|^2 delta;
+ *   ph-e  segments p (all nmodes*N_q phonons), entries (dest electron d, source s) sorted
+ *         by (d, s), weight (4 pi/hbar)(1/N_k)|g|^2 delta;
+ *   ph-ph segments g = a*2 + proc over the M sub-lattice phonons, entries (b, c) sorted by
+ *         (b, c); emission lists unordered pairs b <= c with weight doubled for b != c,
+ *         absorption weight is 2 (36 pi/hbar)(1/N_q,pp)|V3|^2 delta.
+ *   Weights are FP64 on input and stored in the context precision. */
+#define RTBTE_CH_BUILD 0
+#define RTBTE_CH_PREBUILT 1
+typedef struct rtbte_channels {
+    int32_t mode;
+    int32_t reserved;
+    const int64_t *eph_off; const int32_t *eph_src; const int32_t *eph_ph; const double *eph_W;
+    const int64_t *phe_off; const int32_t *phe_dst; const int32_t *phe_src; const double *phe_W;
+    const int64_t *pp_off; const int32_t *pp_b; const int32_t *pp_c; const double *pp_W;
+} rtbte_channels;
+
+/* Per-instance sizes after channels exist. */
+typedef struct rtbte_sizes {
+    int64_t n_c, n_ph, n_pp, y_offset, n_y_total;
+    int64_t eph_entries, phe_entries, pp_entries;        /* logical entries          */
+    int64_t eph_stored, phe_stored, pp_stored;           /* stored, incl. padding    */
+    int64_t work_items;                                  /* whole context            */
+    int64_t channel_bytes;                               /* device bytes, this inst. */
+} rtbte_sizes;
+
+/* ---- integrators (Methods B) --------------------------------------------- */
+#define RTBTE_RK4 0       /* classical RK4, fixed step h                                 */
+#define RTBTE_BS32 1      /* adaptive Bogacki-Shampine 3(2)                              */
+#define RTBTE_ZON43 2     /* adaptive Zonneveld 4(3) (ARKODE's default ERK)               */
+#define RTBTE_MRI_KW3 3   /* MIS on Knoth-Wolke, fixed slow step h_s, adaptive fast ERK  */
+#define RTBTE_SPLIT_RK4 4 /* first-order splitting: RK4 slow step h_s, RK4 fast steps h  */
+
+typedef struct rtbte_integ {
+    int32_t method;        /* RTBTE_RK4 .. RTBTE_SPLIT_RK4                                */
+    int32_t fast_method;   /* inner ERK of MRI: RTBTE_ZON43 (default) or RTBTE_BS32      */
+    double t0;             /* time of the incoming state y                                */
+    double h;              /* RK4 step; SPLIT_RK4 fast step                               */
+    double h_s;            /* MRI / SPLIT_RK4 slow step                                   */
+    double rtol, atol_c, atol_ph;   /* Eq. wrms_weights; atol per carrier / phonon row   */
+    double h0;             /* first step (<= 0: Hairer-Norsett-Wanner estimate)           */
+    double hmin, hmax;     /* 0: unbounded                                                */
+    int64_t max_steps;     /* accepted-step limit per call (0: 10^9)                      */
+    double a1, a2, a3;     /* PID gains (Eq. pid_controller), p* = method order           */
+    int32_t pid_sign_mode; /* 0: eps_k^-a1 eps_{k-1}^+a2 eps_{k-2}^-a3; 1: all negative    */
+    int32_t max_nef;       /* consecutive error-test failures allowed (default 7)         */
+    double safety, growth, growth_first, etamxf, etamin; /* 0: library defaults          */
+    int32_t small_nef;     /* failures before etamxf applies (default 2)                  */
+    int32_t chunk;         /* attempts enqueued between host checks (0: auto)             */
+} rtbte_integ;
+
+typedef struct rtbte_stats {
+    int64_t steps, attempts, fails;      /* accepted steps, attempts, error-test fails    */
+    int64_t rhs_full, rhs_fast, rhs_slow;/* RHS evaluations by part set                   */
+    int64_t slow_steps;                  /* MRI / split slow steps                        */
+    double t;                            /* time of the returned y                        */
+    double h_last, h_next;               /* last accepted step, next proposal             */
+    int32_t status;                      /* same as the return value                      */
+    int32_t reserved;
+} rtbte_stats;
+
+typedef struct rtbte_ctx rtbte_ctx;
+
+/* Fill `d` with defaults (1 instance, FP32_COMP, hbar = 6.582119569e-4 eV*ps, device 0). */
+void rtbte_desc_defaults(rtbte_desc *d);
+/* Fill `o` with the paper's defaults: PID a1=0.58, a2=0.21, a3=0.1 (Methods B) and ARKODE's
+ * documented controller constants for what the paper leaves unstated. */
+void rtbte_integ_defaults(rtbte_integ *o);
+
+/* Create a context: copies the instance tables to the device and allocates the state-size
+ * work buffers.  Errors: INVALID_ARG (bad desc), OOM, CUDA. */
+int rtbte_create(const rtbte_desc *d, rtbte_ctx **out);
+
+/* Build (mode BUILD) or copy (mode PREBUILT) the channel lists of instance `inst`.  Device
+ * builder: one-time enumeration of every (destination, source, mode, process) term whose
+ * energy mismatch is within 3 sigma and whose phonons are above omega_cut; FP64 filter with
+ * IEEE add/sub only, so the lists are bit-identical to any IEEE implementation of the same
+ * rule.  Replaces earlier channels of the instance.  Errors: INVALID_ARG, UNSUPPORTED
+ * (an index does not fit the packed 32-bit entry format), OOM, CUDA. */
+int rtbte_upload_channels(rtbte_ctx *ctx, int inst, const rtbte_channels *ch);
+
+/* ydot = selected parts of the RHS at y (time t is accepted for interface symmetry; the
+ * rt-BTE RHS is autonomous).  y and ydot are FP64 [n_y_total] arrays, either both device
+ * pointers (stream-ordered, asynchronous) or both host pointers (staged through the
+ * context, synchronous).  Rows of parts not selected are written as 0.
+ * Errors: STATE (some instance has no channels), INVALID_ARG, CUDA. */
+int rtbte_rhs(rtbte_ctx *ctx, double t, const double *y, double *ydot, unsigned parts);
+
+/* Advance the device state y (FP64 [n_y_total], caller-owned) from opt->t0 to t_out with
+ * the method of `opt`.  All stepping, error norms and step-size control run on the device;
+ * the host only checks a 4-byte flag between chunks of attempts.  On success y holds the
+ * solution at t_out; on failure y holds the last accepted state and st->t its time.
+ * Synchronises the stream.  Errors: INVALID_ARG, STATE, TOO_MANY_STEPS, STEP_UNDERFLOW,
+ * ERR_TEST_FAIL, NONFINITE, CUDA. */
+int rtbte_advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *opt, rtbte_stats *st);
+
+/* Sizes of instance `inst` (channel counts are 0 before rtbte_upload_channels). */
+int rtbte_get_sizes(const rtbte_ctx *ctx, int inst, rtbte_sizes *out);
+
+/* Copy instance `inst`'s stored lists back to host in the PREBUILT logical order (padding
+ * removed).  which: RTBTE_EPH, RTBTE_PHE or RTBTE_PHPH.  off must hold the segment count
+ * + 1 entries; a/b/W must hold the logical entry count (rtbte_get_sizes).  For e-ph a/b
+ * are (src, phonon); ph-e (dst, src); ph-ph (b, c).  Synchronous. */
+int rtbte_download_channels(rtbte_ctx *ctx, int inst, unsigned which, int64_t *off, int32_t *a, int32_t *b,
+                            double *W);
+
+/* Set the stream used by later calls (cudaStream_t; NULL = default stream). */
+int rtbte_set_stream(rtbte_ctx *ctx, void *stream);
+
+/* Number of kernel launches the library enqueued since the context was created. */
+int64_t rtbte_launch_count(const rtbte_ctx *ctx);
+
+/* Message of the last failure on this context (never NULL). */
+const char *rtbte_last_error(const rtbte_ctx *ctx);
+const char *rtbte_status_string(int status);
+
+/* Release every device and host resource of the context (NULL is ignored). */
+void rtbte_destroy(rtbte_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTBTE_H */

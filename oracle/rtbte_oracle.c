@@ -277,7 +277,7 @@ static long phe_phonon(const or_model *m, const or_aux *a, long p, int32_t *dst,
     int nu = (int)(p / a->Nq);
     int qc[3];
     q_coords(m, p % a->Nq, qc);
-    int cand[8 * 8];
+    int cand[512]; /* up to 3 preimages per dimension times nbands (<= 16) */
     long cnt = 0;
     for (int d = 0; d < m->n_c; ++d) {
         int nc = phe_sources(m, a, d, qc, cand);
@@ -546,7 +546,7 @@ void or_rhs_literal(const or_model *m, const double *y, double *ydot, unsigned p
             int nu = (int)(p / a.Nq);
             int qc[3];
             q_coords(m, p % a.Nq, qc);
-            int cand[64];
+            int cand[512];
             double acc = 0.0;
             for (int d = 0; d < m->n_c; ++d) {
                 int nc = phe_sources(m, &a, d, qc, cand);
@@ -852,6 +852,7 @@ int or_erk_solve(or_rhs_fn fn, void *u, long n, double t0, double t1, double *y,
             first = 0;
             nef = 0;
             st->h_last = hk;
+            if (t < t1 && !(t + h > t)) { status = OR_STEP_UNDERFLOW; break; }
         } else {
             st->fails++;
             nef++;
@@ -861,7 +862,7 @@ int or_erk_solve(or_rhs_fn fn, void *u, long n, double t0, double t1, double *y,
             if (eta > 1.0) eta = 1.0;
             if (nef >= o->small_nef && eta > o->etamxf) eta = o->etamxf;
             h = hk * eta;
-            if (h < o->hmin) { status = OR_STEP_UNDERFLOW; break; }
+            if (h < o->hmin || !(t + h > t)) { status = OR_STEP_UNDERFLOW; break; }
         }
     }
     st->t = t;

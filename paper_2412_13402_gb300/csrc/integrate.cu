@@ -1,0 +1,707 @@
+// integrate.cu -- time integration of the rt-BTE on the device (Methods B).
+//
+// One attempted step of an explicit RK method (Eq. ERK_method) is a fixed kernel sequence:
+//   prep      populations <- y                                  (stage 1: z_1 = y)
+//   S times:  collision kernel (rhs.cu) -> partials per work item
+//             stage kernel: k_i = -sum(partials) [+ MRI forcing];  z_{i+1} = y + h sum_j A_{i+1,j} k_j
+//             written straight into the population copies; after the last stage
+//             y_new = y + h sum b_i k_i, e = h sum (b_i - bt_i) k_i and per-block WRMS partials
+//             of e with weights 1/(rtol |y_{n-1}| + atol_i) (Eqs. wrms_norm, wrms_weights)
+//   controller (one block): WRMS norm in a fixed order, accept if <= 1, PID step proposal
+//             h' = h eps_k^{-a1/p} eps_{k-1}^{+a2/p} eps_{k-2}^{-a3/p} (Eq. pid_controller)
+// Step size, time, error history and which of two state buffers is current live in device
+// memory, so the sequence is captured once into a CUDA graph and replayed; the host only
+// reads a small status block between chunks of attempts.  Readings of what the paper leaves
+// open: PID signs alternate (ARKODE's documented form; the printed all-negative form is
+// pid_sign_mode 1), the other controller constants are ARKODE's documented defaults, the
+// first step follows Hairer-Norsett-Wanner's starting-step algorithm, and the MIS coupling
+// of the last MRI stage is b_j - A_{S,j} (the printed A_{S-1,j} does not reduce MIS to its
+// base method when the fast part vanishes).
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "internal.cuh"
+#include "rows.cuh"
+
+namespace rtbte {
+
+RowParams row_params(rtbte_ctx *ctx);
+
+namespace {
+
+constexpr int kRedThreads = 256;
+
+// ---- Butcher tableaux (as exact fractions in double) --------------------------------
+Tableau tableau_of(int method) {
+    Tableau T;
+    std::memset(&T, 0, sizeof(T));
+    if (method == RTBTE_RK4 || method == RTBTE_SPLIT_RK4) {  // classical RK4
+        T.S = 4; T.p = 4; T.has_emb = 0;
+        T.c[1] = 1.0 / 2; T.c[2] = 1.0 / 2; T.c[3] = 1.0;
+        T.A[1][0] = 1.0 / 2; T.A[2][1] = 1.0 / 2; T.A[3][2] = 1.0;
+        T.b[0] = 1.0 / 6; T.b[1] = 1.0 / 3; T.b[2] = 1.0 / 3; T.b[3] = 1.0 / 6;
+    } else if (method == RTBTE_BS32) {  // Bogacki-Shampine 3(2)
+        T.S = 4; T.p = 3; T.has_emb = 1;
+        T.c[1] = 1.0 / 2; T.c[2] = 3.0 / 4; T.c[3] = 1.0;
+        T.A[1][0] = 1.0 / 2;
+        T.A[2][1] = 3.0 / 4;
+        T.A[3][0] = 2.0 / 9; T.A[3][1] = 1.0 / 3; T.A[3][2] = 4.0 / 9;
+        T.b[0] = 2.0 / 9; T.b[1] = 1.0 / 3; T.b[2] = 4.0 / 9; T.b[3] = 0.0;
+        T.bt[0] = 7.0 / 24; T.bt[1] = 1.0 / 4; T.bt[2] = 1.0 / 3; T.bt[3] = 1.0 / 8;
+    } else {  // Zonneveld 4(3)
+        T.S = 5; T.p = 4; T.has_emb = 1;
+        T.c[1] = 1.0 / 2; T.c[2] = 1.0 / 2; T.c[3] = 1.0; T.c[4] = 3.0 / 4;
+        T.A[1][0] = 1.0 / 2;
+        T.A[2][1] = 1.0 / 2;
+        T.A[3][2] = 1.0;
+        T.A[4][0] = 5.0 / 32; T.A[4][1] = 7.0 / 32; T.A[4][2] = 13.0 / 32; T.A[4][3] = -1.0 / 32;
+        T.b[0] = 1.0 / 6; T.b[1] = 1.0 / 3; T.b[2] = 1.0 / 3; T.b[3] = 1.0 / 6; T.b[4] = 0.0;
+        T.bt[0] = -1.0 / 2; T.bt[1] = 7.0 / 3; T.bt[2] = 7.0 / 3; T.bt[3] = 13.0 / 6; T.bt[4] = -16.0 / 3;
+    }
+    return T;
+}
+
+// Knoth-Wolke 3-stage base of the MIS method and its MRI abscissae / couplings (K = 1).
+struct Mis {
+    double chat[4];
+    double Om[4][3];
+};
+Mis mis_kw3() {
+    const double A[3][3] = {{0, 0, 0}, {1.0 / 3, 0, 0}, {-3.0 / 16, 15.0 / 16, 0}};
+    const double b[3] = {1.0 / 6, 3.0 / 10, 8.0 / 15};
+    const double c[3] = {0, 1.0 / 3, 3.0 / 4};
+    Mis M;
+    std::memset(&M, 0, sizeof(M));
+    for (int i = 0; i < 3; ++i) M.chat[i] = c[i];
+    M.chat[3] = 1.0;
+    for (int i = 1; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M.Om[i][j] = A[i][j] - A[i - 1][j];
+    for (int j = 0; j < 3; ++j) M.Om[3][j] = b[j] - A[2][j];
+    return M;
+}
+
+struct StageArgs {
+    Tableau T;
+    CtlParams cp;
+    Ctl *ctl;
+    double *Y0, *Y1, *K;
+    const double *forcing;
+    double *wrms_part;
+    long long n;
+    unsigned parts;
+    int stage;         // -1: populations <- y; 0..S-1: combine stage `stage`
+    int respect_done;  // inside an attempt sequence: skip once the integration is done
+};
+
+__device__ __forceinline__ double atol_of(const CtlParams &cp, const InstDev &I, long long local) {
+    return local < I.n_c ? cp.atol_c : cp.atol_ph;
+}
+
+__device__ __forceinline__ void block_sum_store(double v, double *dst) {
+    __shared__ double red[kRedThreads];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *dst = red[0];
+}
+
+template <class R>
+__global__ void __launch_bounds__(kRedThreads) stage_kernel(RowParams Q, StageArgs a) {
+    const Ctl *ctl = a.ctl;
+    if (a.respect_done && ctl->done) return;
+    const double *y = ctl->cur ? a.Y1 : a.Y0;
+    double *yn = ctl->cur ? a.Y0 : a.Y1;
+    const double h = ctl->h_try;
+    const int S = a.T.S, i = a.stage;
+    double wsum = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.n; c += (long long)gridDim.x * blockDim.x) {
+        const int ii = Q.n_inst > 1 ? find_inst(Q, c) : 0;
+        const InstDev I = Q.inst[ii];
+        const long long local = c - I.y_off;
+        if (i < 0) {
+            write_pops<R>(Q, I, local, y[c]);
+            continue;
+        }
+        double k = row_value<R>(Q, I, local, a.parts);
+        if (a.forcing) k += a.forcing[c];
+        a.K[(long long)i * a.n + c] = k;
+        if (i < S - 1) {
+            double acc = 0.0;
+            for (int j = 0; j <= i; ++j) acc += a.T.A[i + 1][j] * a.K[(long long)j * a.n + c];
+            write_pops<R>(Q, I, local, y[c] + h * acc);
+        } else {
+            double s1 = 0.0, s2 = 0.0;
+            for (int j = 0; j < S; ++j) {
+                const double kj = a.K[(long long)j * a.n + c];
+                s1 += a.T.b[j] * kj;
+                s2 += (a.T.b[j] - a.T.bt[j]) * kj;
+            }
+            const double ynew = y[c] + h * s1;
+            yn[c] = ynew;
+            if (a.T.has_emb) {
+                const double e = h * s2;
+                const double w = 1.0 / (a.cp.rtol * fabs(y[c]) + atol_of(a.cp, I, local));
+                const double x = e * w;
+                wsum += x * x;
+            }
+            if (!isfinite(ynew)) wsum += __longlong_as_double(0x7ff8000000000000LL);
+        }
+    }
+    if (i == S - 1) block_sum_store(wsum, a.wrms_part + blockIdx.x);
+}
+
+__device__ double reduce_parts(const double *part, int n) {
+    __shared__ double red[kRedThreads];
+    double v = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) v += part[b];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void arm(Ctl *c) {
+    double hk = c->h;
+    c->last = 0;
+    if (c->fixed) {  // classical fixed steps: last step ends exactly at t_out
+        c->last = (c->steps + 1 >= c->max_steps) ? 1 : 0;
+        c->h_try = c->last ? c->t_out - c->t : hk;
+        return;
+    }
+    if (c->t + hk >= c->t_out) {
+        hk = c->t_out - c->t;
+        c->last = 1;
+    }
+    c->h_try = hk;
+}
+
+__global__ void controller_kernel(Ctl *c, CtlParams cp, const double *part, int nparts, long long n) {
+    if (c->done) return;
+    const double sum = reduce_parts(part, nparts);
+    if (threadIdx.x != 0) return;
+    const double eps = sqrt(sum / (double)n);
+    c->attempts++;
+    if (!isfinite(eps)) {
+        c->status = RTBTE_E_NONFINITE;
+        c->done = 1;
+        return;
+    }
+    if (c->fixed) {
+        c->cur ^= 1;
+        c->t = c->last ? c->t_out : c->t + c->h_try;
+        c->steps++;
+        c->h_last = c->h_try;
+        if (c->last) c->done = 1;
+        else arm(c);
+        return;
+    }
+    const double p = (double)cp.p;
+    c->eps = eps;
+    if (eps <= 1.0) {
+        c->cur ^= 1;
+        c->t = c->last ? c->t_out : c->t + c->h_try;
+        c->steps++;
+        const double e = eps > 1e-10 ? eps : 1e-10;
+        double eta = cp.pid_sign_mode == 0 ? pow(e, -cp.a1 / p) * pow(c->eps1, cp.a2 / p) * pow(c->eps2, -cp.a3 / p)
+                                           : pow(e, -cp.a1 / p) * pow(c->eps1, -cp.a2 / p) * pow(c->eps2, -cp.a3 / p);
+        eta *= cp.safety;
+        double cap = c->first ? cp.growth_first : cp.growth;
+        if (c->nef > 0 && cap > 1.0) cap = 1.0;
+        if (eta > cap) eta = cap;
+        double h = c->h_try * eta;
+        if (cp.hmax > 0 && h > cp.hmax) h = cp.hmax;
+        c->h = h;
+        c->eps2 = c->eps1;
+        c->eps1 = e;
+        c->first = 0;
+        c->nef = 0;
+        c->h_last = c->h_try;
+        if (c->t >= c->t_out) {
+            c->done = 1;
+            return;
+        }
+        if (!(c->t + h > c->t)) {  // the proposed step no longer advances time
+            c->status = RTBTE_E_STEP_UNDERFLOW;
+            c->done = 1;
+            return;
+        }
+        if (c->steps - c->steps_base >= c->max_steps) {
+            c->status = RTBTE_E_TOO_MANY_STEPS;
+            c->done = 1;
+            return;
+        }
+    } else {
+        c->fails++;
+        c->nef++;
+        if (c->nef >= cp.max_nef) {
+            c->status = RTBTE_E_ERR_TEST_FAIL;
+            c->done = 1;
+            return;
+        }
+        double eta = cp.safety * pow(eps, -1.0 / p);
+        if (eta < cp.etamin) eta = cp.etamin;
+        if (eta > 1.0) eta = 1.0;
+        if (c->nef >= cp.small_nef && eta > cp.etamxf) eta = cp.etamxf;
+        const double h = c->h_try * eta;
+        c->h = h;
+        if (h < cp.hmin || !(c->t + h > c->t)) {
+            c->status = RTBTE_E_STEP_UNDERFLOW;
+            c->done = 1;
+            return;
+        }
+    }
+    arm(c);
+}
+
+// ---- Hairer-Norsett-Wanner starting step ---------------------------------------------
+__global__ void __launch_bounds__(kRedThreads) h0_norms(RowParams Q, CtlParams cp, const Ctl *ctl, const double *Y0,
+                                                         const double *Y1, const double *K0, const double *K1,
+                                                         double *part, int second, long long n) {
+    const double *y = ctl->cur ? Y1 : Y0;
+    double s0 = 0.0, s1 = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int ii = Q.n_inst > 1 ? find_inst(Q, c) : 0;
+        const InstDev I = Q.inst[ii];
+        const double w = 1.0 / (cp.rtol * fabs(y[c]) + atol_of(cp, I, c - I.y_off));
+        if (!second) {
+            const double a = y[c] * w, b = K0[c] * w;
+            s0 += a * a;
+            s1 += b * b;
+        } else {
+            const double d = (K1[c] - K0[c]) * w;
+            s0 += d * d;
+        }
+    }
+    block_sum_store(s0, part + blockIdx.x);
+    __syncthreads();
+    if (!second) block_sum_store(s1, part + gridDim.x + blockIdx.x);
+}
+
+__global__ void h0_first(Ctl *c, const double *part, int nparts, long long n, double span) {
+    const double s0 = reduce_parts(part, nparts);
+    const double s1 = reduce_parts(part + nparts, nparts);
+    if (threadIdx.x != 0) return;
+    const double d0 = sqrt(s0 / (double)n), d1 = sqrt(s1 / (double)n);
+    double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+    if (h0 > span) h0 = span;
+    c->h0tmp = h0;
+    c->eps = d1;  // kept for the second half
+}
+
+template <class R>
+__global__ void h0_probe(RowParams Q, const Ctl *ctl, const double *Y0, const double *Y1, const double *K0, long long n) {
+    const double *y = ctl->cur ? Y1 : Y0;
+    const double h0 = ctl->h0tmp;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int ii = Q.n_inst > 1 ? find_inst(Q, c) : 0;
+        const InstDev I = Q.inst[ii];
+        write_pops<R>(Q, I, c - I.y_off, y[c] + h0 * K0[c]);
+    }
+}
+
+__global__ void h0_second(Ctl *c, CtlParams cp, const double *part, int nparts, long long n, double span) {
+    const double s = reduce_parts(part, nparts);
+    if (threadIdx.x != 0) return;
+    const double h0 = c->h0tmp, d1 = c->eps;
+    const double d2 = sqrt(s / (double)n) / h0;
+    const double dm = d1 > d2 ? d1 : d2;
+    const double h1 = dm <= 1e-15 ? fmax(1e-6, h0 * 1e-3) : pow(0.01 / dm, 1.0 / (cp.p + 1));
+    double h = 100.0 * h0 < h1 ? 100.0 * h0 : h1;
+    if (h > span) h = span;
+    if (cp.hmax > 0 && h > cp.hmax) h = cp.hmax;
+    c->h = h;
+    c->eps = 0.0;
+    arm(c);
+}
+
+__global__ void arm_kernel(Ctl *c) { arm(c); }
+
+// Inner (fast) ERK restart for an MRI stage: fresh error history, carried step proposal.
+__global__ void mri_stage_reset(Ctl *c, CtlParams cp, double ta, double tb) {
+    c->t = ta;
+    c->t_out = tb;
+    c->eps1 = 1.0;
+    c->eps2 = 1.0;
+    c->first = 1;
+    c->nef = 0;
+    c->done = 0;
+    c->status = 0;
+    c->steps_base = c->steps;
+    double h = c->h;
+    if (h > tb - ta) h = tb - ta;
+    if (cp.hmax > 0 && h > cp.hmax) h = cp.hmax;
+    c->h = h;
+    if (h > 0) arm(c);
+}
+
+// MIS forcing of stage i (Methods B, step 2b with K = 1): r = (1/dc_i) sum_{j<i} Om_ij fs_j
+__global__ void mri_forcing(double *r, const double *Fs, double om0, double om1, double om2, int i, double dc,
+                            long long n) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        const double om[3] = {om0, om1, om2};
+        for (int j = 0; j < i; ++j) acc += om[j] * Fs[(long long)j * n + c];
+        r[c] = acc / dc;
+    }
+}
+
+// ---- host helpers -----------------------------------------------------------------------
+int row_grid(rtbte_ctx *ctx) { return (int)std::min<long long>((ctx->n_y + kRedThreads - 1) / kRedThreads, kWrmsBlocks); }
+
+template <class R>
+int launch_stage(rtbte_ctx *ctx, const StageArgs &a, cudaStream_t s) {
+    stage_kernel<R><<<row_grid(ctx), kRedThreads, 0, s>>>(row_params(ctx), a);
+    RT_CUDA(ctx, cudaGetLastError());
+    ctx->launches++;
+    return RTBTE_OK;
+}
+
+int stage(rtbte_ctx *ctx, const StageArgs &a, cudaStream_t s) {
+    return ctx->precision == RTBTE_PREC_FP64 ? launch_stage<double>(ctx, a, s) : launch_stage<float>(ctx, a, s);
+}
+
+StageArgs stage_args(rtbte_ctx *ctx, const Tableau &T, const CtlParams &cp, unsigned parts, const double *forcing) {
+    StageArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.T = T;
+    a.cp = cp;
+    a.ctl = ctx->ctl.as<Ctl>();
+    a.Y0 = ctx->Y[0].as<double>();
+    a.Y1 = ctx->Y[1].as<double>();
+    a.K = ctx->K.as<double>();
+    a.forcing = forcing;
+    a.wrms_part = ctx->wrms_part.as<double>();
+    a.n = ctx->n_y;
+    a.parts = parts;
+    return a;
+}
+
+// Enqueue one attempted step (prep, S x [collision kernel, stage kernel], controller).
+int enqueue_attempt(rtbte_ctx *ctx, const Tableau &T, const CtlParams &cp, unsigned parts, const double *forcing,
+                    cudaStream_t s) {
+    StageArgs a = stage_args(ctx, T, cp, parts, forcing);
+    a.stage = -1;
+    a.respect_done = 1;
+    int rc;
+    if ((rc = stage(ctx, a, s))) return rc;
+    for (int i = 0; i < T.S; ++i) {
+        if ((rc = launch_rhs_core(ctx, parts, ctx->ctl.as<Ctl>(), s))) return rc;
+        a.stage = i;
+        if ((rc = stage(ctx, a, s))) return rc;
+    }
+    controller_kernel<<<1, kRedThreads, 0, s>>>(ctx->ctl.as<Ctl>(), cp, ctx->wrms_part.as<double>(), row_grid(ctx),
+                                                 ctx->n_y);
+    RT_CUDA(ctx, cudaGetLastError());
+    ctx->launches++;
+    return RTBTE_OK;
+}
+
+long long graph_key(int method, unsigned parts, bool forcing, const CtlParams &cp) {
+    // the controller constants are captured by value: key them by a hash of their bytes
+    unsigned long long h = 1469598103934665603ULL;
+    const unsigned char *b = reinterpret_cast<const unsigned char *>(&cp);
+    for (size_t i = 0; i < sizeof(cp); ++i) h = (h ^ b[i]) * 1099511628211ULL;
+    return (long long)((h & ~0xffffULL) | ((unsigned long long)method << 8) | (parts << 1) | (forcing ? 1 : 0));
+}
+
+// One attempt as a CUDA graph (captured on the private stream, launched on the user stream).
+int attempt_graph(rtbte_ctx *ctx, int method, const CtlParams &cp, unsigned parts, const double *forcing,
+                  cudaGraphExec_t *out, int *nlaunch) {
+    const Tableau T = tableau_of(method);
+    *nlaunch = 2 * T.S + 2;
+    long long key = graph_key(method, parts, forcing != nullptr, cp);
+    auto it = ctx->graphs.find(key);
+    if (it != ctx->graphs.end()) {
+        *out = it->second;
+        return RTBTE_OK;
+    }
+    cudaGraph_t g;
+    long long before = ctx->launches;
+    RT_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_attempt(ctx, T, cp, parts, forcing, ctx->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    ctx->launches = before;  // captured, not executed
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    ctx->graphs[key] = ex;
+    *out = ex;
+    return RTBTE_OK;
+}
+
+int read_ctl(rtbte_ctx *ctx) {
+    RT_CUDA(ctx, cudaMemcpyAsync(ctx->ctl_host, ctx->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return RTBTE_OK;
+}
+
+int write_ctl(rtbte_ctx *ctx) {
+    RT_CUDA(ctx, cudaMemcpyAsync(ctx->ctl.p, ctx->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+    RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return RTBTE_OK;
+}
+
+// Run attempts until the device says done.  Returns a CUDA/launch error code, else RTBTE_OK
+// (the integration status is then in ctx->ctl_host->status).
+int run_attempts(rtbte_ctx *ctx, int method, const CtlParams &cp, unsigned parts, const double *forcing, int chunk,
+                 long long *attempts_out) {
+    cudaGraphExec_t ex;
+    int nl, rc;
+    if ((rc = attempt_graph(ctx, method, cp, parts, forcing, &ex, &nl))) return rc;
+    long long a0 = ctx->ctl_host->attempts;
+    for (;;) {
+        for (int k = 0; k < chunk; ++k) {
+            RT_CUDA(ctx, cudaGraphLaunch(ex, ctx->stream));
+            ctx->launches += nl;
+        }
+        if ((rc = read_ctl(ctx))) return rc;
+        if (ctx->ctl_host->done) break;
+    }
+    if (attempts_out) *attempts_out = ctx->ctl_host->attempts - a0;
+    return RTBTE_OK;
+}
+
+// Hairer-Norsett-Wanner first step; 2 RHS evaluations of `parts` (+ forcing).
+int h0_estimate(rtbte_ctx *ctx, const CtlParams &cp, unsigned parts, const double *forcing, double span) {
+    const int nb = row_grid(ctx);
+    RowParams Q = row_params(ctx);
+    Ctl *c = ctx->ctl.as<Ctl>();
+    double *K0 = ctx->K.as<double>(), *K1 = K0 + ctx->n_y;
+    StageArgs a = stage_args(ctx, tableau_of(RTBTE_ZON43), cp, parts, forcing);
+    a.stage = -1;
+    int rc;
+    if ((rc = stage(ctx, a, ctx->stream))) return rc;
+    if ((rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) return rc;
+    if ((rc = launch_rows(ctx, parts, K0, forcing, ctx->stream))) return rc;
+    h0_norms<<<nb, kRedThreads, 0, ctx->stream>>>(Q, cp, c, ctx->Y[0].as<double>(), ctx->Y[1].as<double>(), K0, K1,
+                                                  ctx->wrms_part.as<double>(), 0, ctx->n_y);
+    h0_first<<<1, kRedThreads, 0, ctx->stream>>>(c, ctx->wrms_part.as<double>(), nb, ctx->n_y, span);
+    if (ctx->precision == RTBTE_PREC_FP64)
+        h0_probe<double><<<nb, kRedThreads, 0, ctx->stream>>>(Q, c, ctx->Y[0].as<double>(), ctx->Y[1].as<double>(), K0,
+                                                              ctx->n_y);
+    else
+        h0_probe<float><<<nb, kRedThreads, 0, ctx->stream>>>(Q, c, ctx->Y[0].as<double>(), ctx->Y[1].as<double>(), K0,
+                                                             ctx->n_y);
+    RT_CUDA(ctx, cudaGetLastError());
+    ctx->launches += 3;
+    if ((rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) return rc;
+    if ((rc = launch_rows(ctx, parts, K1, forcing, ctx->stream))) return rc;
+    h0_norms<<<nb, kRedThreads, 0, ctx->stream>>>(Q, cp, c, ctx->Y[0].as<double>(), ctx->Y[1].as<double>(), K0, K1,
+                                                  ctx->wrms_part.as<double>(), 1, ctx->n_y);
+    h0_second<<<1, kRedThreads, 0, ctx->stream>>>(c, cp, ctx->wrms_part.as<double>(), nb, ctx->n_y, span);
+    RT_CUDA(ctx, cudaGetLastError());
+    ctx->launches += 2;
+    return RTBTE_OK;
+}
+
+CtlParams ctl_params(const rtbte_integ *o, int p) {
+    CtlParams cp;
+    std::memset(&cp, 0, sizeof(cp));
+    cp.rtol = o->rtol;
+    cp.atol_c = o->atol_c;
+    cp.atol_ph = o->atol_ph;
+    cp.a1 = o->a1;
+    cp.a2 = o->a2;
+    cp.a3 = o->a3;
+    cp.safety = o->safety > 0 ? o->safety : 0.96;
+    cp.growth = o->growth > 0 ? o->growth : 20.0;
+    cp.growth_first = o->growth_first > 0 ? o->growth_first : 1e4;
+    cp.etamxf = o->etamxf > 0 ? o->etamxf : 0.3;
+    cp.etamin = o->etamin > 0 ? o->etamin : 0.1;
+    cp.hmin = o->hmin;
+    cp.hmax = o->hmax;
+    cp.p = p;
+    cp.pid_sign_mode = o->pid_sign_mode;
+    cp.small_nef = o->small_nef > 0 ? o->small_nef : 2;
+    cp.max_nef = o->max_nef > 0 ? o->max_nef : 7;
+    return cp;
+}
+
+void ctl_reset(Ctl *c, double t0, double t_out) {
+    std::memset(c, 0, sizeof(Ctl));
+    c->t = t0;
+    c->t_out = t_out;
+    c->eps1 = c->eps2 = 1.0;
+    c->first = 1;
+}
+
+// Fixed-step RK4 of `parts` over [t0, t1] with nominal step h (last step ends at t1).
+int fixed_rk4(rtbte_ctx *ctx, const rtbte_integ *o, unsigned parts, double t0, double t1, double h,
+              long long *attempts) {
+    Ctl *ch = ctx->ctl_host;
+    int rc;
+    if ((rc = read_ctl(ctx))) return rc;
+    const int cur = ch->cur;
+    ctl_reset(ch, t0, t1);
+    ch->cur = cur;
+    ch->fixed = 1;
+    ch->h = h;
+    ch->max_steps = (long long)ceil((t1 - t0) / h - 1e-9);
+    if (ch->max_steps < 1) ch->max_steps = 1;
+    ch->last = ch->max_steps == 1;
+    ch->h_try = ch->last ? t1 - t0 : h;
+    if ((rc = write_ctl(ctx))) return rc;
+    CtlParams cp = ctl_params(o, 4);
+    return run_attempts(ctx, RTBTE_RK4, cp, parts, nullptr, o->chunk > 0 ? o->chunk : 8, attempts);
+}
+
+}  // namespace
+
+int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rtbte_stats *st) {
+    rtbte_stats local;
+    if (!st) st = &local;
+    std::memset(st, 0, sizeof(*st));
+    const int m = o->method;
+    if (m < RTBTE_RK4 || m > RTBTE_SPLIT_RK4) return fail(ctx, RTBTE_E_INVALID_ARG, "unknown method");
+    if (!(t_out > o->t0)) return fail(ctx, RTBTE_E_INVALID_ARG, "t_out must exceed t0");
+    if ((m == RTBTE_RK4 || m == RTBTE_SPLIT_RK4) && !(o->h > 0)) return fail(ctx, RTBTE_E_INVALID_ARG, "h must be > 0");
+    if ((m == RTBTE_MRI_KW3 || m == RTBTE_SPLIT_RK4) && !(o->h_s > 0))
+        return fail(ctx, RTBTE_E_INVALID_ARG, "h_s must be > 0");
+    if ((m == RTBTE_BS32 || m == RTBTE_ZON43 || m == RTBTE_MRI_KW3) &&
+        (!(o->rtol >= 0) || !(o->atol_c > 0) || !(o->atol_ph > 0)))
+        return fail(ctx, RTBTE_E_INVALID_ARG, "tolerances must be positive");
+    const size_t nb = sizeof(double) * ctx->n_y;
+    RT_CUDA(ctx, cudaMemcpyAsync(ctx->Y[0].p, y, nb, cudaMemcpyDeviceToDevice, ctx->stream));
+    Ctl *ch = ctx->ctl_host;
+    int rc = RTBTE_OK;
+    ctl_reset(ch, o->t0, t_out);
+    ch->max_steps = o->max_steps > 0 ? o->max_steps : 1000000000LL;
+    if (m == RTBTE_RK4) {
+        if ((rc = write_ctl(ctx))) return rc;
+        long long att = 0;
+        if ((rc = fixed_rk4(ctx, o, RTBTE_ALL, o->t0, t_out, o->h, &att))) return rc;
+        st->attempts = att;
+        st->rhs_full = 4 * att;
+        st->steps = ch->steps;
+    } else if (m == RTBTE_BS32 || m == RTBTE_ZON43) {
+        const Tableau T = tableau_of(m);
+        CtlParams cp = ctl_params(o, T.p);
+        const bool est = !(o->h0 > 0);
+        if (!est) ch->h = o->hmax > 0 && o->h0 > o->hmax ? o->hmax : o->h0;
+        if ((rc = write_ctl(ctx))) return rc;
+        if (est) {
+            if ((rc = h0_estimate(ctx, cp, RTBTE_ALL, nullptr, t_out - o->t0))) return rc;
+        } else {
+            arm_kernel<<<1, 1, 0, ctx->stream>>>(ctx->ctl.as<Ctl>());
+            RT_CUDA(ctx, cudaGetLastError());
+            ctx->launches++;
+        }
+        long long att = 0;
+        if ((rc = run_attempts(ctx, m, cp, RTBTE_ALL, nullptr, o->chunk > 0 ? o->chunk : 8, &att))) return rc;
+        st->attempts = att;
+        st->rhs_full = att * T.S + (est ? 2 : 0);
+        st->steps = ch->steps;
+    } else if (m == RTBTE_MRI_KW3) {
+        const Mis M = mis_kw3();
+        const int fm = o->fast_method == RTBTE_BS32 ? RTBTE_BS32 : RTBTE_ZON43;
+        const Tableau Tf = tableau_of(fm);
+        CtlParams cp = ctl_params(o, Tf.p);
+        ch->h = 0.0;
+        if ((rc = write_ctl(ctx))) return rc;
+        const long long n = ctx->n_y;
+        double *Fs = ctx->Fs.as<double>();
+        double *r = ctx->forcing.as<double>();
+        const int nb2 = row_grid(ctx);
+        long long nsteps = (long long)ceil((t_out - o->t0) / o->h_s - 1e-9);
+        if (nsteps < 1) nsteps = 1;
+        double t = o->t0;
+        bool first_inner = true;
+        long long inner_attempts = 0, inner_h0 = 0;
+        StageArgs a = stage_args(ctx, Tf, cp, RTBTE_SLOW, nullptr);
+        a.stage = -1;
+        a.respect_done = 0;
+        for (long long k = 0; k < nsteps; ++k) {
+            const double H = (k == nsteps - 1) ? t_out - t : o->h_s;
+            // slow RHS at z_1 = y
+            if ((rc = stage(ctx, a, ctx->stream))) return rc;
+            if ((rc = launch_rhs_core(ctx, RTBTE_SLOW, nullptr, ctx->stream))) return rc;
+            if ((rc = launch_rows(ctx, RTBTE_SLOW, Fs, nullptr, ctx->stream))) return rc;
+            st->rhs_slow++;
+            for (int i = 1; i <= 3; ++i) {
+                const double dc = M.chat[i] - M.chat[i - 1];
+                const double ta = t + M.chat[i - 1] * H, tb = (i == 3) ? t + H : t + M.chat[i] * H;
+                mri_forcing<<<nb2, kRedThreads, 0, ctx->stream>>>(r, Fs, M.Om[i][0], M.Om[i][1], M.Om[i][2], i, dc, n);
+                mri_stage_reset<<<1, 1, 0, ctx->stream>>>(ctx->ctl.as<Ctl>(), cp, ta, tb);
+                RT_CUDA(ctx, cudaGetLastError());
+                ctx->launches += 2;
+                if (first_inner) {
+                    if ((rc = h0_estimate(ctx, cp, RTBTE_FAST, r, tb - ta))) return rc;
+                    inner_h0++;
+                    first_inner = false;
+                }
+                long long att = 0;
+                if ((rc = run_attempts(ctx, fm, cp, RTBTE_FAST, r, o->chunk > 0 ? o->chunk : 4, &att))) return rc;
+                inner_attempts += att;
+                if (ch->status != RTBTE_OK) break;
+                if (i < 3) {
+                    if ((rc = stage(ctx, a, ctx->stream))) return rc;
+                    if ((rc = launch_rhs_core(ctx, RTBTE_SLOW, nullptr, ctx->stream))) return rc;
+                    if ((rc = launch_rows(ctx, RTBTE_SLOW, Fs + (long long)i * n, nullptr, ctx->stream))) return rc;
+                    st->rhs_slow++;
+                }
+            }
+            if (ch->status != RTBTE_OK) break;
+            t = (k == nsteps - 1) ? t_out : t + H;
+            st->slow_steps++;
+        }
+        st->attempts = inner_attempts;
+        st->rhs_fast = inner_attempts * Tf.S + 2 * inner_h0;
+        st->steps = ch->steps;
+        if (ch->status == RTBTE_OK) ch->t = t;
+    } else {  // first-order operator splitting with RK4 (slow step, then fast sub-steps)
+        if ((rc = write_ctl(ctx))) return rc;
+        long long nsteps = (long long)ceil((t_out - o->t0) / o->h_s - 1e-9);
+        if (nsteps < 1) nsteps = 1;
+        double t = o->t0;
+        long long att_s = 0, att_f = 0;
+        for (long long k = 0; k < nsteps; ++k) {
+            const double H = (k == nsteps - 1) ? t_out - t : o->h_s;
+            long long a1 = 0, a2 = 0;
+            if ((rc = fixed_rk4(ctx, o, RTBTE_SLOW, t, t + H, H, &a1))) return rc;
+            att_s += a1;
+            if (ch->status != RTBTE_OK) break;
+            long long msub = (long long)floor(H / o->h + 0.5);
+            if (msub < 1) msub = 1;
+            if ((rc = fixed_rk4(ctx, o, RTBTE_FAST, t, t + H, H / (double)msub, &a2))) return rc;
+            att_f += a2;
+            st->steps += ch->steps;
+            if (ch->status != RTBTE_OK) break;
+            t = (k == nsteps - 1) ? t_out : t + H;
+            st->slow_steps++;
+        }
+        st->attempts = att_s + att_f;
+        st->rhs_slow = 4 * att_s;
+        st->rhs_fast = 4 * att_f;
+        if (ch->status == RTBTE_OK) ch->t = t;
+    }
+    st->fails = ch->fails;
+    st->t = ch->t;
+    st->h_last = ch->h_last;
+    st->h_next = ch->h;
+    // hand back the current buffer (the solution, or the last accepted state on failure)
+    RT_CUDA(ctx, cudaMemcpyAsync(y, ctx->Y[ch->cur].p, nb, cudaMemcpyDeviceToDevice, ctx->stream));
+    RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    st->status = ch->status;
+    if (st->status) fail(ctx, st->status, "integration stopped before t_out");
+    return st->status;
+}
+
+void destroy_graphs(rtbte_ctx *ctx) {
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+}
+
+}  // namespace rtbte

@@ -1,0 +1,223 @@
+// internal.cuh -- declarations shared by the translation units of librtbte.
+//
+// Data layout in HBM (one context, several independent instances):
+//   state y (FP64, caller-owned)   [inst0: f (n_c) | N (nmodes*N_q)] [inst1: ...] ...
+//   population copies (compute precision R, written once per RHS by the stage kernels):
+//     popf  electron f per instance, padded to a multiple of 4 elements
+//     popN  phonon N per instance as [mode][q] with the q stride padded to a multiple of 4,
+//           so the slice of one mode is a 16-byte aligned block for staging
+//     popP  N on the ph-ph sub-lattice (compact index a = nu*N_q,pp + qs_lin), padded
+//   channel lists (per instance, per part): uint32 packed index + weight (R), CSR offsets
+//     e-ph  segments (nu, d, proc) -> idx = s | q << s_bits     (q = phonon q_lin of mode nu)
+//     ph-e  segments p             -> idx = d | s << s_bits
+//     ph-ph segments (a, proc)     -> idx = b | c << pp_bits
+//     every segment is padded with zero-weight entries to a multiple of 4 entries so that a
+//     warp reads 4 entries per lane with one 16-byte load.
+//   work items: <= 512 entries of one segment, processed by one warp, which writes one
+//   compensated partial sum (hi, lo); rows combine their items' partials in item order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "rtbte.h"
+
+namespace rtbte {
+
+constexpr int kItemEntries = 512;  // 32 lanes x 4 vectors x 4 entries
+constexpr int kSegPad = 4;
+constexpr int kRhsThreads = 512;
+constexpr int kMaxModes = 16;
+constexpr int kMaxStages = 5;
+constexpr int kWrmsBlocks = 512;
+
+enum { PART_EPH = 0, PART_PHE = 1, PART_PP = 2 };
+
+struct __align__(16) Item {
+    long long begin;      // first entry, relative to the group's entry arrays
+    int dest;             // instance-local destination (electron d, phonon p, sub-lattice a)
+    unsigned short len;   // entries (multiple of 4, <= kItemEntries)
+    unsigned char proc;   // 0 emission, 1 absorption
+    unsigned char pad;
+};
+
+// Consecutive items that share one shared-memory staging of populations.
+struct __align__(16) Group {
+    const uint32_t *idx;  // entry arrays of this instance and part
+    const void *W;
+    int item_begin, item_end;
+    int part, inst, nu, s_bits;
+    int pp_bits, n_q_pad;
+    int stage0_len, stage1_len;  // staged element counts (multiples of 4)
+    long long stage0_src;        // popf (e-ph, ph-e) or popP (ph-ph) offset of the staged block
+    long long stage1_src;        // popN offset of the staged mode slice (e-ph)
+    long long f_inst, N_inst, P_inst;  // instance offsets in popf / popN / popP
+};
+
+// Per-instance layout used by the row kernels.
+struct __align__(16) InstDev {
+    long long y_off;
+    int n_c, n_ph, M, nmodes;
+    int N_q, N_q_pad, pad0, pad1;
+    long long f_off, N_off, P_off;  // offsets in popf / popN / popP
+    long long eoff_base;            // item offsets of e-ph rows: [nmodes][n_c+1]
+    long long poff_base;            // item offsets of ph-e rows: [n_ph+1]
+    long long ppoff_base;           // item offsets of ph-ph rows: [M+1]
+    long long compact_base;         // sub-lattice index of each phonon (-1: none): [n_ph]
+};
+
+// Device-side controller state of the adaptive integrators (one per context).
+struct __align__(16) Ctl {
+    double t, t_out, h, h_try;
+    double eps, eps1, eps2, h_last;
+    double h0tmp, span_t0, pad_d0, pad_d1;
+    long long steps, attempts, fails, rhs;
+    long long max_steps, steps_base, pad_l0, pad_l1;
+    int first, nef, done, status;
+    int cur, last, fixed, pad_i0;
+};
+
+struct CtlParams {  // constants of one integration (captured into graphs by value)
+    double rtol, atol_c, atol_ph;
+    double a1, a2, a3, safety, growth, growth_first, etamxf, etamin, hmin, hmax;
+    int p, pid_sign_mode, small_nef, max_nef;
+};
+
+struct Tableau {
+    int S, p, has_emb, pad;
+    double A[kMaxStages][kMaxStages];
+    double b[kMaxStages], bt[kMaxStages], c[kMaxStages];
+};
+
+// ---- small device helpers -------------------------------------------------
+__host__ __device__ inline int wrapi(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+__host__ __device__ inline int min_image(int d, int n) {
+    d = wrapi(d, n);
+    return d > n / 2 ? d - n : d;
+}
+// SplitMix64 output function (Steele, Lea & Flood 2014), used as a keyed hash.
+__host__ __device__ inline unsigned long long mix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+inline int bits_for(long long n) {  // bits needed for indices 0..n-1
+    int b = 1;
+    while ((1LL << b) < n) ++b;
+    return b;
+}
+inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+// ---- device buffer ----------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// Builder input tables of one instance on the device.
+struct BuildTables {
+    const int4 *ek;                       // (kx, ky, kz, band) per electron state
+    const double *eps;                    // [n_c]
+    const unsigned long long *eid, *eid_inv;  // electron grid ids of k and -k
+    const double *omega;                  // [nmodes*N_q]
+    const int *kmap;                      // [nbands*N_k] state index or -1
+    const double *lut;                    // [2^lut_bits]
+    const double *g2;                     // [nmodes]
+    const int *pp_full, *pp_full_inv;     // [M] full phonon index of a and of its -q image
+    int n_c, nbands, nmodes, fold, lut_bits;
+    int nk[3], nq[3], nqs[3];
+    long long N_k, N_q, N_ph, M, N_qs;
+    int s_bits, q_bits, pp_bits;
+    double cut_eph, cut_pp, sigma_eph, sigma_pp, omega_cut;
+    double pref_eph, pref_phe, pref_pp;  // 2pi/(hbar N_q), 4pi/(hbar N_k), 36pi/(hbar N_q,pp)
+    double v3;
+    unsigned long long g2_seed, v3_seed;
+};
+
+struct InstHost {
+    rtbte_instance_desc d{};
+    std::vector<int32_t> e_band, e_k;
+    std::vector<double> e_eps, ph_omega, lut, g2_coef;
+    long long N_k = 0, N_q = 0, n_ph = 0, M = 0, N_qs = 0;
+    int nqs[3] = {1, 1, 1};
+    int N_q_pad = 0, n_c_pad = 0, M_pad = 0;
+    int s_bits = 0, q_bits = 0, pp_bits = 0;
+    std::vector<int32_t> pp_full, pp_full_inv, compact;
+    // builder tables (device), kept for rebuilds
+    DevBuf t_ek, t_eps, t_eid, t_eidinv, t_omega, t_kmap, t_lut, t_g2, t_ppfull, t_ppinv;
+    // channel lists (device)
+    DevBuf eph_idx, eph_W, phe_idx, phe_W, pp_idx, pp_W;
+    std::vector<long long> eph_off, phe_off, pp_off;  // padded CSR offsets (host copy)
+    std::vector<long long> eph_cnt, phe_cnt, pp_cnt;  // logical counts per segment
+    bool has_channels = false;
+    long long y_off = 0, f_off = 0, N_off = 0, P_off = 0;
+};
+
+}  // namespace rtbte
+
+struct rtbte_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int precision = RTBTE_PREC_FP32_COMP;
+    size_t real_size = 4;
+    double hbar = 6.582119569e-4;
+    std::vector<rtbte::InstHost> inst;
+    long long n_y = 0;
+    long long popf_len = 0, popN_len = 0, popP_len = 0;
+    rtbte::DevBuf popf, popN, popP, instdev, compact;
+    // execution plan of the RHS
+    bool plan_valid = false;
+    rtbte::DevBuf items, groups, partials, eoff, poff, ppoff, cta_tab;
+    int n_items = 0, n_groups = 0;
+    int part_items[3] = {0, 0, 0};
+    int part_first[3] = {0, 0, 0};
+    int grid = 0, threads = rtbte::kRhsThreads;
+    size_t smem_bytes = 0;
+    bool staged = false;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    // integrator work buffers
+    rtbte::DevBuf Y[2], K, Fs, forcing, wrms_part, ctl, ystage, ydstage;
+    rtbte::Ctl *ctl_host = nullptr;  // pinned mirror for status reads
+    std::map<long long, cudaGraphExec_t> graphs;
+    long long launches = 0;
+    std::string err;
+};
+
+namespace rtbte {
+// builder.cu
+int build_channels(rtbte_ctx *ctx, int inst);
+int upload_tables(rtbte_ctx *ctx, int inst);
+// rhs.cu
+int make_plan(rtbte_ctx *ctx);
+int launch_prep_from_y(rtbte_ctx *ctx, const double *y, cudaStream_t s);
+int launch_rhs_core(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStream_t s);
+int launch_rows(rtbte_ctx *ctx, unsigned parts, double *out, const double *forcing, cudaStream_t s);
+// integrate.cu
+int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *opt, rtbte_stats *st);
+void destroy_graphs(rtbte_ctx *ctx);
+// api.cu
+int fail(rtbte_ctx *ctx, int code, const std::string &msg);
+int cuda_fail(rtbte_ctx *ctx, cudaError_t e, const char *what);
+}  // namespace rtbte
+
+#define RT_CUDA(ctx, call)                                         \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return rtbte::cuda_fail(ctx, e_, #call); \
+    } while (0)

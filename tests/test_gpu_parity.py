@@ -1,0 +1,332 @@
+"""GPU parity of librtbte against the FP64 CPU oracle, through the C ABI.
+
+Channel lists: indices and offsets bit-exact, weights within one FP32 ulp (FP32 storage)
+or 1e-14 relative (FP64 storage; the two sides' exp() may differ in the last bit).
+RHS: relative L2 <= 1e-5 in FP32_COMP mode, <= 1e-12 in FP64 mode.
+Integrated populations: relative L2 <= 1e-6 (FP32 collision sums) or tighter in FP64.
+"""
+import numpy as np
+import pytest
+
+import rtbte_inputs as ri
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPH, PHE, PHPH, FAST, SLOW, ALL = 1, 2, 4, 3, 4, 7
+
+
+@pytest.fixture(scope="module")
+def rt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_13402_gb300 import build
+
+    build.build()
+    import paper_2412_13402_gb300 as m
+
+    return m
+
+
+def relL2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def sym_state(m, seed):
+    f, N = ri.random_populations(m, seed)
+    nx, ny, nz = m.nq
+    q = np.arange(m.N_q)
+    x, y, z = q % nx, (q // nx) % ny, q // (nx * ny)
+    qi = ((-z % nz) * ny + (-y % ny)) * nx + (-x % nx)
+    inv = (np.arange(m.nmodes)[:, None] * m.N_q + qi[None, :]).ravel()
+    N = 0.5 * (N + N[inv])
+    return np.concatenate([f, N])
+
+
+def mode_blocked(m, L):
+    """Oracle e-ph lists (segments (d, proc), entries by (mode, src)) regrouped into segments
+    (mode, d, proc)."""
+    off = L["off"]
+    seg = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    nu = L["ph"] // m.N_q
+    d, proc = seg // 2, seg % 2
+    key = (nu * m.n_c + d) * 2 + proc
+    order = np.argsort(key, kind="stable")
+    cnt = np.bincount(key, minlength=2 * m.nmodes * m.n_c)
+    o = np.zeros(cnt.size + 1, np.int64)
+    np.cumsum(cnt, out=o[1:])
+    return dict(off=o, a=L["src"][order], b=L["ph"][order], W=L["W"][order])
+
+
+def assert_w_close(got, want, fp64):
+    if fp64:
+        assert np.all(np.abs(got - want) <= 1e-14 * np.abs(want))
+    else:
+        # FP32 storage: within one ulp of the FP64 value (round-to-nearest plus exp's last bit)
+        assert np.all(np.abs(got - want) <= 2.0 ** -23 * np.abs(want))
+
+
+MODELS = {
+    "tiny2d": lambda: ri.tiny((4, 4, 1)),
+    "tiny3d_fold2": lambda: ri.tiny((4, 4, 4), fold=2, nbands=2, nmodes=2, pp_stride=1),
+    "tiny2d_pp2": lambda: ri.tiny((6, 6, 1), pp_stride=2, sigma_pp=0.03),
+    "toy2d": lambda: ri.toy2d(),
+    "ladder": lambda: ri.ladder(n=6),
+    "graphene36": lambda: ri.graphene_small(36),
+}
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("name", list(MODELS))
+def test_channel_lists_match_oracle(rt, oracle_lib, name, prec):
+    m = MODELS[name]()
+    ctx = rt.Context(m, precision=prec)
+    ctx.upload_channels()
+    o = oracle_lib.Oracle(m)
+    L = o.build_lists()
+    want = mode_blocked(m, L["eph"])
+    got = ctx.download_channels(0, rt.RTBTE_EPH)
+    assert np.array_equal(got["off"], want["off"])
+    assert np.array_equal(got["a"], want["a"]) and np.array_equal(got["b"], want["b"])
+    assert_w_close(got["W"], want["W"], prec == "fp64")
+    got = ctx.download_channels(0, rt.RTBTE_PHE)
+    assert np.array_equal(got["off"], L["phe"]["off"])
+    assert np.array_equal(got["a"], L["phe"]["dst"]) and np.array_equal(got["b"], L["phe"]["src"])
+    assert_w_close(got["W"], L["phe"]["W"], prec == "fp64")
+    if m.pp_stride > 0:
+        got = ctx.download_channels(0, rt.RTBTE_PHPH)
+        assert np.array_equal(got["off"], L["pp"]["off"])
+        assert np.array_equal(got["a"], L["pp"]["b"]) and np.array_equal(got["b"], L["pp"]["c"])
+        assert_w_close(got["W"], L["pp"]["W"], prec == "fp64")
+    s = ctx.sizes(0)
+    assert s["eph_entries"] == L["eph"]["off"][-1] and s["eph_stored"] % 4 == 0
+    ctx.close()
+
+
+@pytest.mark.parametrize("parts", [ALL, EPH, PHE, PHPH, FAST])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp64", 1e-12)])
+@pytest.mark.parametrize("name", ["tiny3d_fold2", "tiny2d_pp2", "toy2d", "graphene36"])
+def test_rhs_matches_oracle(rt, oracle_lib, name, prec, tol, parts):
+    m = MODELS[name]()
+    ctx = rt.Context(m, precision=prec)
+    ctx.upload_channels()
+    o = oracle_lib.Oracle(m)
+    o.build_lists()
+    for y in (m.y0(), sym_state(m, 3), np.concatenate(ri.random_populations(m, 9))):
+        ref = o.rhs(y, parts)
+        got = ctx.rhs(torch.tensor(y, device="cuda")).cpu().numpy()
+        if np.linalg.norm(ref) == 0:
+            assert np.abs(got).max() == 0
+        else:
+            assert relL2(got, ref) <= tol, (name, prec, parts)
+        # rows of parts not requested are exactly zero
+        if not parts & EPH:
+            assert not got[: m.n_c].any()
+    ctx.close()
+
+
+def test_prebuilt_upload_equals_device_build(rt, oracle_lib):
+    m = ri.graphene_small(36)
+    o = oracle_lib.Oracle(m)
+    L = o.build_lists()
+    a = rt.Context(m)
+    a.upload_channels()
+    b = rt.Context(m)
+    b.upload_channels(prebuilt=L)
+    y = torch.tensor(sym_state(m, 2), device="cuda")
+    ra, rb = a.rhs(y).cpu().numpy(), b.rhs(y).cpu().numpy()
+    assert relL2(rb, ra) < 1e-6
+    assert relL2(rb, o.rhs(y.cpu().numpy())) < 1e-5
+    a.close()
+    b.close()
+
+
+def test_rhs_host_pointers_and_determinism(rt):
+    m = ri.graphene_small(36)
+    ctx = rt.Context(m)
+    ctx.upload_channels()
+    y = sym_state(m, 5)
+    dev = ctx.rhs(torch.tensor(y, device="cuda")).cpu().numpy()
+    dev2 = ctx.rhs(torch.tensor(y, device="cuda")).cpu().numpy()
+    host = ctx.rhs(torch.tensor(y)).numpy()
+    assert np.array_equal(dev, dev2)
+    assert np.array_equal(dev, host)
+    ctx.close()
+
+
+def test_batched_instances_equal_single_contexts(rt):
+    ms = [ri.graphene_small(24), ri.graphene_small(36, seed=5), ri.graphene(n=30, window=0.6, seed=77)]
+    ctx = rt.Context(ms)
+    for i in range(len(ms)):
+        ctx.upload_channels(i)
+    ys = [sym_state(m, 10 + i) for i, m in enumerate(ms)]
+    got = ctx.rhs(torch.tensor(np.concatenate(ys), device="cuda")).cpu().numpy()
+    off = 0
+    for i, m in enumerate(ms):
+        c1 = rt.Context(m)
+        c1.upload_channels()
+        one = c1.rhs(torch.tensor(ys[i], device="cuda")).cpu().numpy()
+        assert np.array_equal(got[off:off + m.n_y], one)
+        assert ctx.sizes(i)["y_offset"] == off
+        off += m.n_y
+        c1.close()
+    ctx.close()
+
+
+def test_full_graphene_workload_sampled(rt, oracle_lib):
+    """The 180 x 180 graphene-like workload in the launch configuration the benchmark uses:
+    sampled channel segments bit-exact and sampled RHS rows within 1e-5 of the literal sums."""
+    m = ri.graphene()
+    ctx = rt.Context(m, precision="fp32")
+    ctx.upload_channels()
+    o = oracle_lib.Oracle(m)
+    rng = np.random.default_rng(0)
+    s = ctx.sizes(0)
+    assert 0.8e8 < s["eph_entries"] < 2e8 and s["pp_entries"] > 1e7
+    # e-ph segments of sampled destinations (mode-blocked on the device)
+    dests = np.sort(rng.choice(m.n_c, 24, replace=False)).astype(np.int32)
+    got = ctx.download_channels(0, rt.RTBTE_EPH)
+    Lo = o.eph_lists(dests=dests)
+    for i, d in enumerate(dests):
+        for proc in (0, 1):
+            sl = slice(Lo["off"][2 * i + proc], Lo["off"][2 * i + proc + 1])
+            src, ph, W = Lo["src"][sl], Lo["ph"][sl], Lo["W"][sl]
+            for nu in range(m.nmodes):
+                sel = (ph // m.N_q) == nu
+                g = (nu * m.n_c + d) * 2 + proc
+                gs = slice(got["off"][g], got["off"][g + 1])
+                assert np.array_equal(got["a"][gs], src[sel]) and np.array_equal(got["b"][gs], ph[sel])
+                assert_w_close(got["W"][gs], W[sel], False)
+    del got
+    phon = np.sort(rng.choice(m.n_ph, 48, replace=False))
+    got = ctx.download_channels(0, rt.RTBTE_PHE)
+    Lo = o.phe_lists(phonons=phon)
+    for i, p in enumerate(phon):
+        gs = slice(got["off"][p], got["off"][p + 1])
+        ls = slice(Lo["off"][i], Lo["off"][i + 1])
+        assert np.array_equal(got["a"][gs], Lo["dst"][ls]) and np.array_equal(got["b"][gs], Lo["src"][ls])
+        assert_w_close(got["W"][gs], Lo["W"][ls], False)
+    del got
+    pd = np.sort(rng.choice(m.n_pp, 16, replace=False))
+    got = ctx.download_channels(0, rt.RTBTE_PHPH)
+    Lo = o.pp_lists(dests=pd)
+    for i, a in enumerate(pd):
+        gs = slice(got["off"][2 * a], got["off"][2 * a + 2])
+        ls = slice(Lo["off"][2 * i], Lo["off"][2 * i + 2])
+        assert np.array_equal(got["a"][gs], Lo["b"][ls]) and np.array_equal(got["b"][gs], Lo["c"][ls])
+        assert_w_close(got["W"][gs], Lo["W"][ls], False)
+    del got
+    # sampled RHS rows vs the literal definition
+    y = m.y0()
+    gpu = ctx.rhs(torch.tensor(y, device="cuda")).cpu().numpy()
+    emask = np.zeros(m.n_c, np.uint8)
+    emask[dests] = 1
+    full = o.pp_full_index()
+    prow = np.unique(np.concatenate([phon, full[pd]]))
+    pmask = np.zeros(m.n_ph, np.uint8)
+    pmask[prow] = 1
+    ref = o.rhs_literal(y, ALL, emask, pmask)
+    rows = np.concatenate([dests, m.n_c + prow])
+    assert relL2(gpu[rows], ref[rows]) <= 1e-5
+    assert relL2(gpu[dests], ref[dests]) <= 1e-5
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# integrators
+# ---------------------------------------------------------------------------
+def test_rk4_and_bs32_toy_fp64(rt, oracle_lib):
+    m = ri.toy2d()
+    o = oracle_lib.Oracle(m)
+    o.build_lists()
+    ctx = rt.Context(m, precision="fp64")
+    ctx.upload_channels()
+    y = torch.tensor(m.y0(), device="cuda")
+    st = ctx.advance_to(0.1, y, method="rk4", t0=0.0, h=0.005)
+    yo, sto = o.rk4(m.y0(), 0.0, 0.1, 0.005)
+    assert st["status"] == 0 and st["steps"] == sto["steps"] == 20 and st["rhs_full"] == 80
+    assert relL2(y.cpu().numpy(), yo) < 1e-12
+    y = torch.tensor(m.y0(), device="cuda")
+    st = ctx.advance_to(0.1, y, method="bs32", t0=0.0, rtol=1e-8, atol_c=1e-15, atol_ph=1e-15)
+    yo, sto = o.erk(m.y0(), 0.0, 0.1, method=oracle_lib.BS32, rtol=1e-8, atol_c=1e-15, atol_ph=1e-15)
+    assert st["status"] == 0 and abs(st["t"] - 0.1) == 0
+    assert st["steps"] == sto["steps"] and st["fails"] == sto["fails"]
+    assert st["rhs_full"] == sto["rhs_evals"]
+    assert relL2(y.cpu().numpy(), yo) < 1e-11
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("fp64", 1e-11)])
+def test_zonneveld_and_mri_graphene(rt, oracle_lib, prec, tol):
+    m = ri.graphene_small(36)
+    o = oracle_lib.Oracle(m)
+    o.build_lists()
+    ctx = rt.Context(m, precision=prec)
+    ctx.upload_channels()
+    kw = dict(rtol=1e-5, atol_c=1e-9, atol_ph=1e-12)
+    y = torch.tensor(m.y0(), device="cuda")
+    st = ctx.advance_to(0.03, y, method="zon43", t0=0.0, **kw)
+    yo, sto = o.erk(m.y0(), 0.0, 0.03, method=oracle_lib.ZON43, **kw)
+    assert st["status"] == 0
+    assert relL2(y.cpu().numpy(), yo) < tol
+    if prec == "fp64":
+        assert st["steps"] == sto["steps"] and st["rhs_full"] == sto["rhs_evals"]
+    y = torch.tensor(m.y0(), device="cuda")
+    st = ctx.advance_to(0.03, y, method="mri", t0=0.0, h_s=0.01, **kw)
+    yo, sto = o.mri(m.y0(), 0.0, 0.03, 0.01, **kw)
+    assert st["status"] == 0 and st["slow_steps"] == 3 and st["rhs_slow"] == 9 == sto["rhs_slow"]
+    assert relL2(y.cpu().numpy(), yo) < tol
+    if prec == "fp64":
+        assert st["steps"] == sto["steps"] and st["rhs_fast"] == sto["rhs_evals"]
+    ctx.close()
+
+
+def test_split_rk4_graphene_fp64(rt, oracle_lib):
+    m = ri.graphene_small(24)
+    o = oracle_lib.Oracle(m)
+    o.build_lists()
+    ctx = rt.Context(m, precision="fp64")
+    ctx.upload_channels()
+    y = torch.tensor(m.y0(), device="cuda")
+    st = ctx.advance_to(0.02, y, method="split_rk4", t0=0.0, h_s=0.005, h=0.001)
+    yo, sto = o.split_rk4(m.y0(), 0.0, 0.02, 0.005, 0.001)
+    assert st["status"] == 0 and st["slow_steps"] == 4
+    assert relL2(y.cpu().numpy(), yo) < 1e-12
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# edge cases and failure statuses (host-side and bounded; nothing faults the GPU)
+# ---------------------------------------------------------------------------
+def test_no_channels_gives_zero_rhs(rt):
+    m = ri.tiny((4, 4, 1), sigma_eph=1e-9, sigma_pp=1e-9)
+    ctx = rt.Context(m)
+    ctx.upload_channels()
+    s = ctx.sizes(0)
+    assert s["eph_entries"] == 0 and s["pp_entries"] == 0
+    got = ctx.rhs(torch.tensor(m.y0(), device="cuda")).cpu().numpy()
+    assert not got.any()
+    ctx.close()
+
+
+def test_status_codes(rt):
+    m = ri.graphene_small(24)
+    ctx = rt.Context(m)
+    y = torch.tensor(m.y0(), device="cuda")
+    with pytest.raises(rt.RtbteError) as e:
+        ctx.rhs(y)
+    assert e.value.code == -9  # no channels yet
+    ctx.upload_channels()
+    with pytest.raises(rt.RtbteError) as e:
+        ctx.rhs(y, parts=0)
+    assert e.value.code == -1
+    with pytest.raises(rt.RtbteError) as e:
+        ctx.advance_to(0.0, y, method="zon43", t0=0.0)
+    assert e.value.code == -1
+    st = ctx.advance_to(1.0, y, method="zon43", t0=0.0, max_steps=2)
+    assert st["rc"] == -4 and st["steps"] == 2 and st["t"] < 1.0
+    bad = y.clone()
+    bad[3] = float("nan")
+    st = ctx.advance_to(0.01, bad, method="zon43", t0=0.0)
+    assert st["rc"] == -7
+    ctx.close()

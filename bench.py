@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark of the rt-BTE right-hand side inside the adaptive integrator on GB300.
+
+Workload: the graphene-like 2D workload (two Dirac bands on a 180 x 180 k-grid within a
+1 eV window, six phonon branches on the same q-grid, three-phonon processes on the 60 x 60
+sub-lattice, 0.5 eV hot-carrier pulse), synthetic inputs from rtbte_inputs.
+
+Step: one call of rtbte_advance_to that advances the device state by a fixed window of
+simulated time with the adaptive Zonneveld 4(3) ERK (rtol 1e-5, atol_c 1e-9, atol_ph 1e-12),
+evaluating the full RHS (e-ph + ph-e + ph-ph) at every stage, the fused stage/WRMS kernels
+and the device controller.  value = full RHS evaluations per second over the timed steps
+(rejected attempts included, they are evaluated).  The channel lists (~2.3 GB) are far
+larger than L2, so every evaluation streams them from HBM; the populations they gather
+are staged in shared memory by design.
+
+Extra fields: roofline of the collision kernel (CUDA events around each launch on the
+library stream, standalone evaluations), e2e (the same windows with the state copied from
+pinned host memory and back every step), MRI simulated ps/s, clocks sampled during the
+timed region, and the FP64 CPU oracle timed on a bounded sample of rows.
+
+`--impl reference` times the CPU oracle alone (the reference arm of this project).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rt-BTE RHS evals/s"
+UNIT = "RHS evals/s"
+WINDOW_PS = 0.005           # simulated time per step (5 fs)
+TOL = dict(rtol=1e-5, atol_c=1e-9, atol_ph=1e-12)
+WORKLOAD = "graphene-like 2D: 2 Dirac bands on 180x180 k-grid (1 eV window, 12722 states), 6 phonon branches " \
+           "on 180x180 q-grid (194400 states), ph-ph on 60x60 sub-lattice, 0.5 eV hot-carrier pulse"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling case: only standalone full-RHS evaluations (warm-up + steps), no JSON line")
+    ap.add_argument("--grid", type=int, default=180, help="k/q grid side of the graphene-like workload (profiling)")
+    return ap.parse_args()
+
+
+def run_profile(args):
+    """Standalone collision-kernel launches for ncu captures: `--warmup` then `--steps` full-RHS
+    evaluations of the graphene-like workload at grid side `--grid`."""
+    import torch
+
+    import paper_2412_13402_gb300 as rt
+    import rtbte_inputs as ri
+
+    m = ri.graphene(n=args.grid)
+    ctx = rt.Context(m, precision="fp32")
+    ctx.upload_channels()
+    y = torch.tensor(m.y0(), device="cuda")
+    yd = torch.empty_like(y)
+    for _ in range(args.warmup):
+        ctx.rhs(y, yd)
+    torch.cuda.synchronize()
+    ctx.set_kernel_timing(True)
+    for _ in range(args.steps):
+        ctx.rhs(y, yd)
+    ms, n = ctx.kernel_time()
+    s = ctx.sizes(0)
+    print(f"profile grid={args.grid} entries={s['eph_entries'] + s['phe_entries'] + s['pp_entries']} "
+          f"rhs_kernel_avg_ms={ms / max(n, 1):.4f}", flush=True)
+    ctx.close()
+    return 0
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample of rows (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample_rate(model, y, seed=0, ne=192, nphe=1536, npp=192):
+    """Full-RHS evaluations per second of the FP64 oracle's literal sums, from timing the
+    three row families on random samples and scaling each to its full row count."""
+    import numpy as np
+
+    import oracle
+
+    o = oracle.Oracle(model)
+    rng = np.random.default_rng(seed)
+    n_c, n_ph = model.n_c, model.n_ph
+    live = np.flatnonzero(~model.frozen())
+    full = o.pp_full_index()
+    live_pp = np.flatnonzero(~model.frozen()[full])
+    ne, nphe, npp = min(ne, n_c), min(nphe, live.size), min(npp, live_pp.size)
+    none_e, none_p = np.zeros(n_c, np.uint8), np.zeros(n_ph, np.uint8)
+    em = none_e.copy()
+    em[rng.choice(n_c, ne, replace=False)] = 1
+    pm = none_p.copy()
+    pm[rng.choice(live, nphe, replace=False)] = 1
+    pp = none_p.copy()
+    pp[full[rng.choice(live_pp, npp, replace=False)]] = 1
+    t0 = time.perf_counter()
+    o.rhs_literal(y, oracle.EPH, em, none_p)
+    t1 = time.perf_counter()
+    o.rhs_literal(y, oracle.PHE, none_e, pm)
+    t2 = time.perf_counter()
+    o.rhs_literal(y, oracle.PHPH, none_e, pp)
+    t3 = time.perf_counter()
+    per_rhs = (t1 - t0) / ne * n_c + (t2 - t1) / nphe * live.size + (t3 - t2) / npp * live_pp.size
+    sample = (f"literal FP64 sums (Eq. e-ph, Eq. ph-ph) for {ne} electron rows, {nphe} ph-e phonon rows and "
+              f"{npp} ph-ph sub-lattice rows of the 180x180 graphene-like workload, each family scaled to its "
+              f"full row count; {t3 - t0:.1f} s wall")
+    return 1.0 / per_rhs, oracle.threads(), sample, t3 - t0
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import rtbte_inputs as ri
+
+    m = ri.graphene()
+    y = m.y0()
+    for _ in range(args.warmup):
+        oracle_sample_rate(m, y, seed=100, ne=24, nphe=192, npp=24)
+    rates, walls = [], []
+    for k in range(args.steps):
+        r, cores, sample, wall = oracle_sample_rate(m, y, seed=k, ne=48, nphe=384, npp=48)
+        rates.append(r)
+        walls.append(wall)
+    total_wall = sum(walls)
+    value = len(rates) / sum(1.0 / r for r in rates)  # evaluations per second over the K samples
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_wall / len(rates),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "oracle": "FP64 CPU oracle, literal collision sums, OpenMP"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, pw, reasons = [], None, [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+                pw.append(float(p[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "samples": len(sm),
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
+
+
+def traffic_from_profile(kernel_src):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    path = os.path.join(ROOT, "profiles", "rhs_kernel_graphene180_dram.txt")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("rhs_cu_sha256_16") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, local_rank, world = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    import paper_2412_13402_gb300 as rt
+    import rtbte_inputs as ri
+
+    m = ri.graphene()
+    ctx = rt.Context(m, precision="fp32", device=local_rank)
+    ctx.upload_channels()
+    sz = ctx.sizes(0)
+    stream = ctx.stream
+    y = torch.tensor(m.y0(), device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- warm-up windows (also settles the step size past t = 0)
+    t = 0.0
+    h0 = 0.0
+    for _ in range(args.warmup):
+        st = ctx.advance_to(t + WINDOW_PS, y, method="zon43", t0=t, h0=h0, **TOL)
+        assert st["status"] == 0, st
+        t, h0 = st["t"], st["h_next"]
+
+    # ---- timed windows
+    barrier()
+    n_rhs = 0
+    launches0 = ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    phys = os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]
+    with ClockSampler(phys) as clk:
+        e0.record(stream)
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            st = ctx.advance_to(t + WINDOW_PS, y, method="zon43", t0=t, h0=h0, **TOL)
+            assert st["status"] == 0, st
+            t, h0 = st["t"], st["h_next"]
+            n_rhs += st["rhs_full"]
+        e1.record(stream)
+        barrier()
+        wall = time.perf_counter() - wall0
+    ms = e0.elapsed_time(e1)
+    launches = ctx.launch_count() - launches0
+    sim_ps = args.steps * WINDOW_PS
+    tot_rhs, tmax = n_rhs, ms
+    if dist is not None:
+        v = torch.tensor([float(n_rhs)], device=dev)
+        dist.all_reduce(v)
+        tot_rhs = v.item()
+        v = torch.tensor([ms], device=dev)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        tmax = v.item()
+    value = tot_rhs / (tmax / 1000.0)
+
+    # ---- roofline: collision kernel alone, CUDA events on the library stream
+    ctx.set_kernel_timing(True)
+    yk = y.clone()
+    yd = torch.empty_like(yk)
+    ctx.kernel_time()
+    for _ in range(max(20, args.steps)):
+        ctx.rhs(yk, yd)
+    kms, kn = ctx.kernel_time()
+    ctx.set_kernel_timing(False)
+    avg_s = kms / kn / 1000.0
+    entries = sz["eph_entries"] + sz["phe_entries"] + sz["pp_entries"]
+    alg_bytes = 8.0 * entries
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = alg_bytes / avg_s / 1e9
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2412_13402_gb300", "csrc", "rhs.cu"))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "rhs_kernel (full RHS: e-ph + ph-e + ph-ph)",
+                "avg_launch_ms": avg_s * 1000.0, "launches_timed": kn, "alg_bytes_per_launch": alg_bytes,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured" if peaks else "fallback"}
+
+    # ---- e2e: state from pinned host memory and back every step
+    yh = torch.empty(y.numel(), dtype=torch.float64, pin_memory=True)
+    yh.copy_(y)
+    barrier()
+    e_rhs = 0
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        f0.record(stream)
+        for _ in range(args.steps):
+            y.copy_(yh, non_blocking=True)
+            st = ctx.advance_to(t + WINDOW_PS, y, method="zon43", t0=t, h0=h0, **TOL)
+            assert st["status"] == 0, st
+            t, h0 = st["t"], st["h_next"]
+            e_rhs += st["rhs_full"]
+            yh.copy_(y, non_blocking=True)
+        f1.record(stream)
+    barrier()
+    e2e_ms = f0.elapsed_time(f1)
+    e2e = {"value": e_rhs / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": 8 * y.numel(),
+           "d2h_bytes_per_step": 8 * y.numel()}
+
+    # ---- MRI (fast e-ph, slow ph-ph), simulated ps per second
+    mri_steps = max(3, args.steps // 8)
+    hs = 0.020
+    barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    st = ctx.advance_to(t + mri_steps * hs, y, method="mri", t0=t, h_s=hs, **TOL)
+    g1.record(stream)
+    barrier()
+    assert st["status"] == 0, st
+    mri_ms = g0.elapsed_time(g1)
+    mri = {"sim_ps_per_s": mri_steps * hs / (mri_ms / 1000.0), "h_s_fs": hs * 1000, "slow_steps": st["slow_steps"],
+           "rhs_fast": st["rhs_fast"], "rhs_slow": st["rhs_slow"], "fast_steps": st["steps"], "ms": mri_ms}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            r, cores, sample, _ = oracle_sample_rate(m, m.y0())
+            cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD,
+                           "step": f"rtbte_advance_to over {WINDOW_PS * 1000:.0f} fs, adaptive Zonneveld 4(3), "
+                                   "rtol 1e-5, atol_c 1e-9, atol_ph 1e-12, full RHS per stage",
+                           "precision": "FP32 collision sums (compensated); FP64 state, stages, WRMS, controller",
+                           "l2": "no flush: channel lists (%.2f GB) exceed L2 (129 MB) and stream from HBM each "
+                                 "evaluation; populations are shared-memory staged by design" % (
+                                     sz["channel_bytes"] / 1e9),
+                           "channel_entries": entries, "replicas": world, "parallelism": f"replicas x{world}"},
+                "sim_ps_per_s": sim_ps * world / (tmax / 1000.0), "rhs_evals_timed": tot_rhs,
+                "roofline": roofline, "e2e": e2e, "mri": mri, "clocks": clk.summary(), "gpu_launches": launches,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.profile:
+        return run_profile(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -226,6 +226,14 @@ int rtbte_download_channels(rtbte_ctx *ctx, int inst, unsigned which, int64_t *o
 /* Set the stream used by later calls (cudaStream_t; NULL = default stream). */
 int rtbte_set_stream(rtbte_ctx *ctx, void *stream);
 
+/* Kernel timing.  While enabled, every launch of the collision kernel enqueued outside a
+ * CUDA graph (rtbte_rhs and the first-step estimate) is bracketed by CUDA events recorded on
+ * the context stream.  rtbte_kernel_time synchronises the stream and returns the summed
+ * device time (ms) and the number of timed launches since the previous query (then resets).
+ * rtbte_advance_to replays graphs and is not timed.  Errors: INVALID_ARG, CUDA. */
+int rtbte_set_kernel_timing(rtbte_ctx *ctx, int enable);
+int rtbte_kernel_time(rtbte_ctx *ctx, double *total_ms, int64_t *launches);
+
 /* Number of kernel launches the library enqueued since the context was created. */
 int64_t rtbte_launch_count(const rtbte_ctx *ctx);
 

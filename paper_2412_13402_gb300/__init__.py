@@ -34,7 +34,8 @@ HBAR_EV_PS = 6.582119569e-4
 
 EXPORTS = ["rtbte_desc_defaults", "rtbte_integ_defaults", "rtbte_create", "rtbte_upload_channels", "rtbte_rhs",
            "rtbte_advance_to", "rtbte_get_sizes", "rtbte_download_channels", "rtbte_set_stream",
-           "rtbte_launch_count", "rtbte_last_error", "rtbte_status_string", "rtbte_destroy"]
+           "rtbte_set_kernel_timing", "rtbte_kernel_time", "rtbte_launch_count", "rtbte_last_error",
+           "rtbte_status_string", "rtbte_destroy"]
 
 
 class InstanceDesc(C.Structure):
@@ -112,6 +113,8 @@ def load():
         L.rtbte_get_sizes.argtypes = [vp, i32, vp]
         L.rtbte_download_channels.argtypes = [vp, i32, C.c_uint, vp, vp, vp, vp]
         L.rtbte_set_stream.argtypes = [vp, vp]
+        L.rtbte_set_kernel_timing.argtypes = [vp, i32]
+        L.rtbte_kernel_time.argtypes = [vp, vp, vp]
         L.rtbte_launch_count.argtypes = [vp]
         L.rtbte_launch_count.restype = i64
         L.rtbte_last_error.argtypes = [vp]
@@ -293,6 +296,15 @@ class Context:
         d = st.as_dict()
         d["rc"] = rc
         return d
+
+    def set_kernel_timing(self, enable: bool):
+        _check(self.ctx, load().rtbte_set_kernel_timing(self.ctx, int(bool(enable))))
+
+    def kernel_time(self):
+        """(summed milliseconds, launches) of collision-kernel launches timed since the last query."""
+        ms, n = C.c_double(), C.c_int64()
+        _check(self.ctx, load().rtbte_kernel_time(self.ctx, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
     def launch_count(self) -> int:
         return int(load().rtbte_launch_count(self.ctx))

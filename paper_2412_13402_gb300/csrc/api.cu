@@ -428,6 +428,29 @@ int rtbte_set_stream(rtbte_ctx *ctx, void *stream) {
     return RTBTE_OK;
 }
 
+int rtbte_set_kernel_timing(rtbte_ctx *ctx, int enable) {
+    if (!ctx) return RTBTE_E_INVALID_ARG;
+    ctx->timing = enable != 0;
+    return RTBTE_OK;
+}
+
+int rtbte_kernel_time(rtbte_ctx *ctx, double *total_ms, int64_t *launches) {
+    if (!ctx || !total_ms || !launches) return RTBTE_E_INVALID_ARG;
+    RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    double tot = 0.0;
+    for (auto &pr : ctx->ev_pending) {
+        float ms = 0.f;
+        RT_CUDA(ctx, cudaEventElapsedTime(&ms, pr.first, pr.second));
+        tot += ms;
+        ctx->ev_pool.push_back(pr.first);
+        ctx->ev_pool.push_back(pr.second);
+    }
+    *total_ms = tot;
+    *launches = (int64_t)ctx->ev_pending.size();
+    ctx->ev_pending.clear();
+    return RTBTE_OK;
+}
+
 int64_t rtbte_launch_count(const rtbte_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 const char *rtbte_last_error(const rtbte_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -462,6 +485,11 @@ void rtbte_destroy(rtbte_ctx *ctx) {
                       &ctx->partials, &ctx->eoff, &ctx->poff, &ctx->ppoff, &ctx->cta_tab, &ctx->Y[0], &ctx->Y[1],
                       &ctx->K, &ctx->Fs, &ctx->forcing, &ctx->wrms_part, &ctx->ctl, &ctx->ystage, &ctx->ydstage};
     for (DevBuf *b : bufs) b->release();
+    for (auto &pr : ctx->ev_pending) {
+        ctx->ev_pool.push_back(pr.first);
+        ctx->ev_pool.push_back(pr.second);
+    }
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;

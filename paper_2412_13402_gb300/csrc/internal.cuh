@@ -196,6 +196,10 @@ struct rtbte_ctx {
     rtbte::Ctl *ctl_host = nullptr;  // pinned mirror for status reads
     std::map<long long, cudaGraphExec_t> graphs;
     long long launches = 0;
+    // collision-kernel timing (events recorded around launches outside graphs)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;            // free events
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
     std::string err;
 };
 

@@ -479,6 +479,23 @@ static int launch_core_t(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStr
     P.popN = ctx->popN.p;
     P.popP = ctx->popP.p;
     P.ctl = ctl;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->timing) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        RT_CUDA(ctx, cudaStreamIsCapturing(s, &cs));
+        if (cs == cudaStreamCaptureStatusNone) {
+            for (cudaEvent_t *e : {&e0, &e1}) {
+                if (ctx->ev_pool.empty()) {
+                    cudaEvent_t ne;
+                    RT_CUDA(ctx, cudaEventCreate(&ne));
+                    ctx->ev_pool.push_back(ne);
+                }
+                *e = ctx->ev_pool.back();
+                ctx->ev_pool.pop_back();
+            }
+            RT_CUDA(ctx, cudaEventRecord(e0, s));
+        }
+    }
     if (ctx->staged) {
         rhs_kernel<R, true, 1><<<ctx->grid, ctx->threads, ctx->smem_bytes, s>>>(P);
     } else {
@@ -486,6 +503,10 @@ static int launch_core_t(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStr
     }
     RT_CUDA(ctx, cudaGetLastError());
     ctx->launches++;
+    if (e0) {
+        RT_CUDA(ctx, cudaEventRecord(e1, s));
+        ctx->ev_pending.push_back({e0, e1});
+    }
     return RTBTE_OK;
 }
 

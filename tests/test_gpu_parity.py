@@ -114,7 +114,7 @@ def test_rhs_matches_oracle(rt, oracle_lib, name, prec, tol, parts):
     o.build_lists()
     for y in (m.y0(), sym_state(m, 3), np.concatenate(ri.random_populations(m, 9))):
         ref = o.rhs(y, parts)
-        got = ctx.rhs(torch.tensor(y, device="cuda")).cpu().numpy()
+        got = ctx.rhs(torch.tensor(y, device="cuda"), parts=parts).cpu().numpy()
         if np.linalg.norm(ref) == 0:
             assert np.abs(got).max() == 0
         else:
@@ -242,9 +242,9 @@ def test_rk4_and_bs32_toy_fp64(rt, oracle_lib):
     ctx = rt.Context(m, precision="fp64")
     ctx.upload_channels()
     y = torch.tensor(m.y0(), device="cuda")
-    st = ctx.advance_to(0.1, y, method="rk4", t0=0.0, h=0.005)
-    yo, sto = o.rk4(m.y0(), 0.0, 0.1, 0.005)
-    assert st["status"] == 0 and st["steps"] == sto["steps"] == 20 and st["rhs_full"] == 80
+    st = ctx.advance_to(0.1, y, method="rk4", t0=0.0, h=0.001)
+    yo, sto = o.rk4(m.y0(), 0.0, 0.1, 0.001)
+    assert st["status"] == 0 and st["steps"] == sto["steps"] == 100 and st["rhs_full"] == 400
     assert relL2(y.cpu().numpy(), yo) < 1e-12
     y = torch.tensor(m.y0(), device="cuda")
     st = ctx.advance_to(0.1, y, method="bs32", t0=0.0, rtol=1e-8, atol_c=1e-15, atol_ph=1e-15)
@@ -278,6 +278,20 @@ def test_zonneveld_and_mri_graphene(rt, oracle_lib, prec, tol):
     assert relL2(y.cpu().numpy(), yo) < tol
     if prec == "fp64":
         assert st["steps"] == sto["steps"] and st["rhs_fast"] == sto["rhs_evals"]
+    ctx.close()
+
+
+def test_rk4_beyond_its_stability_limit_reports_nonfinite(rt):
+    """Fixed-step RK4 diverges when h is too long (Results: RK4 diverges for h > 5 fs on graphene);
+    on the toy model 5 fs is past the limit and the device controller stops with NONFINITE,
+    handing back the last finite state."""
+    m = ri.toy2d()
+    ctx = rt.Context(m, precision="fp64")
+    ctx.upload_channels()
+    y = torch.tensor(m.y0(), device="cuda")
+    st = ctx.advance_to(0.1, y, method="rk4", t0=0.0, h=0.005)
+    assert st["rc"] == -7 and 0 < st["t"] < 0.1
+    assert torch.isfinite(y).all()
     ctx.close()
 
 

@@ -241,6 +241,32 @@ int64_t rtbte_launch_count(const rtbte_ctx *ctx);
 const char *rtbte_last_error(const rtbte_ctx *ctx);
 const char *rtbte_status_string(int status);
 
+/* ---- allocation-free e-ph RHS ----------------------------------------------------------
+ * The paper has no counterpart to this entry point.  It exists for callers that cannot
+ * allocate device memory: code running while a CUDA graph is being captured (cudaMalloc is
+ * not allowed there, or is not recorded into the graph), programs whose device memory is
+ * owned by another allocator or a pre-reserved arena, and latency-critical loops where an
+ * allocation's implicit synchronisation is not acceptable.  It needs no context and calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Writes ydot[0..n_c) = I^{e-ph} (the electron rows of one instance) from caller-owned
+ * device arrays: y (FP64 [n_c + n_ph], the instance's state vector) and the e-ph channel
+ * list in the layout rtbte_download_channels(RTBTE_EPH) returns -- off (int64
+ * [2*nmodes*n_c + 1], segment (nu*n_c + d)*2 + proc), src (int32 source electron), ph (int32
+ * full phonon index, < n_ph), W (FP64 weights) -- into ydot (FP64 [n_c]).  Arithmetic as in
+ * RTBTE_PREC_FP32_COMP.  Working memory is one fixed array of RTBTE_NOALLOC_SCRATCH_BYTES in
+ * the library's device image (held by every device that loads the library until exit);
+ * sizes needing more (4 B per state row, each part rounded up to 16 B, plus 8 B per list
+ * segment) are rejected with RTBTE_E_UNSUPPORTED before any work.  The first call on a
+ * device looks that array up (cudaGetSymbolAddress, which may load the library's device
+ * code): make it before any stream capture on that device.  All calls on a device share the
+ * array, so calls that can overlap on the GPU (other streams, other host threads) race:
+ * serialise them.  Enqueued on `stream` (a cudaStream_t), asynchronous.
+ * Errors: INVALID_ARG (bad size or NULL pointer), UNSUPPORTED (too large), CUDA. */
+#define RTBTE_NOALLOC_SCRATCH_BYTES (8u << 20)
+int rtbte_eph_rhs_noalloc(int32_t n_c, int64_t n_ph, int32_t nmodes, const int64_t *off, const int32_t *src,
+                          const int32_t *ph, const double *W, const double *y, double *ydot, void *stream);
+
 /* Release every device and host resource of the context (NULL is ignored). */
 void rtbte_destroy(rtbte_ctx *ctx);
 

@@ -35,7 +35,7 @@ HBAR_EV_PS = 6.582119569e-4
 EXPORTS = ["rtbte_desc_defaults", "rtbte_integ_defaults", "rtbte_create", "rtbte_upload_channels", "rtbte_rhs",
            "rtbte_advance_to", "rtbte_get_sizes", "rtbte_download_channels", "rtbte_set_stream",
            "rtbte_set_kernel_timing", "rtbte_kernel_time", "rtbte_launch_count", "rtbte_last_error",
-           "rtbte_status_string", "rtbte_destroy"]
+           "rtbte_status_string", "rtbte_eph_rhs_noalloc", "rtbte_destroy"]
 
 
 class InstanceDesc(C.Structure):
@@ -121,6 +121,7 @@ def load():
         L.rtbte_last_error.restype = C.c_char_p
         L.rtbte_status_string.argtypes = [i32]
         L.rtbte_status_string.restype = C.c_char_p
+        L.rtbte_eph_rhs_noalloc.argtypes = [C.c_int32, i64, C.c_int32, vp, vp, vp, vp, vp, vp, vp]
         L.rtbte_destroy.argtypes = [vp]
         L.rtbte_destroy.restype = None
         _lib = L

@@ -226,6 +226,14 @@ int rtbte_download_channels(rtbte_ctx *ctx, int inst, unsigned which, int64_t *o
 /* Set the stream used by later calls (cudaStream_t; NULL = default stream). */
 int rtbte_set_stream(rtbte_ctx *ctx, void *stream);
 
+/* Autotuner of the collision kernel's work split.  The persistent launch divides the work
+ * items among CTAs by weight = entries + w per item, w being the fixed cost of an item in
+ * entry equivalents; this call times the kernel for `parts` with several w and keeps the
+ * fastest (returned in *chosen when not NULL).  Synchronises the stream; results of later
+ * calls do not depend on the choice (rows add item partials in a fixed order).
+ * Errors: INVALID_ARG, STATE, CUDA. */
+int rtbte_autotune(rtbte_ctx *ctx, unsigned parts, int *chosen);
+
 /* Kernel timing.  While enabled, every launch of the collision kernel enqueued outside a
  * CUDA graph (rtbte_rhs and the first-step estimate) is bracketed by CUDA events recorded on
  * the context stream.  rtbte_kernel_time synchronises the stream and returns the summed

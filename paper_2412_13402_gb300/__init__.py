@@ -34,7 +34,7 @@ HBAR_EV_PS = 6.582119569e-4
 
 EXPORTS = ["rtbte_desc_defaults", "rtbte_integ_defaults", "rtbte_create", "rtbte_upload_channels", "rtbte_rhs",
            "rtbte_advance_to", "rtbte_get_sizes", "rtbte_download_channels", "rtbte_set_stream",
-           "rtbte_set_kernel_timing", "rtbte_kernel_time", "rtbte_launch_count", "rtbte_last_error",
+           "rtbte_autotune", "rtbte_set_kernel_timing", "rtbte_kernel_time", "rtbte_launch_count", "rtbte_last_error",
            "rtbte_status_string", "rtbte_eph_rhs_noalloc", "rtbte_destroy"]
 
 
@@ -113,6 +113,7 @@ def load():
         L.rtbte_get_sizes.argtypes = [vp, i32, vp]
         L.rtbte_download_channels.argtypes = [vp, i32, C.c_uint, vp, vp, vp, vp]
         L.rtbte_set_stream.argtypes = [vp, vp]
+        L.rtbte_autotune.argtypes = [vp, C.c_uint, vp]
         L.rtbte_set_kernel_timing.argtypes = [vp, i32]
         L.rtbte_kernel_time.argtypes = [vp, vp, vp]
         L.rtbte_launch_count.argtypes = [vp]
@@ -297,6 +298,12 @@ class Context:
         d = st.as_dict()
         d["rc"] = rc
         return d
+
+    def autotune(self, parts: int = RTBTE_ALL) -> int:
+        """Pick the collision kernel's work-split weight by timing; returns the chosen weight."""
+        w = C.c_int()
+        _check(self.ctx, load().rtbte_autotune(self.ctx, parts, C.byref(w)))
+        return w.value
 
     def set_kernel_timing(self, enable: bool):
         _check(self.ctx, load().rtbte_set_kernel_timing(self.ctx, int(bool(enable))))

@@ -428,6 +428,15 @@ int rtbte_set_stream(rtbte_ctx *ctx, void *stream) {
     return RTBTE_OK;
 }
 
+int rtbte_autotune(rtbte_ctx *ctx, unsigned parts, int *chosen) {
+    if (!ctx) return RTBTE_E_INVALID_ARG;
+    if (parts == 0 || parts > RTBTE_ALL) return fail(ctx, RTBTE_E_INVALID_ARG, "bad parts");
+    int rc;
+    if ((rc = ensure_plan(ctx))) return rc;
+    destroy_graphs(ctx);  // graphs keep the previous split's table pointer
+    return autotune(ctx, parts, chosen);
+}
+
 int rtbte_set_kernel_timing(rtbte_ctx *ctx, int enable) {
     if (!ctx) return RTBTE_E_INVALID_ARG;
     ctx->timing = enable != 0;

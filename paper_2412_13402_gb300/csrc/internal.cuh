@@ -187,6 +187,9 @@ struct rtbte_ctx {
     int part_items[3] = {0, 0, 0};
     int part_first[3] = {0, 0, 0};
     int grid = 0, threads = rtbte::kRhsThreads;
+    std::vector<unsigned short> item_len_h;  // entries per work item (host copy for re-splitting)
+    int item_overhead = 320;                 // work-split weight of an item beyond its entries
+    double part_scale[3] = {1.0, 1.0, 1.0};  // relative cost of an entry of each part
     size_t smem_bytes = 0;
     bool staged = false;
     int num_sms = 0;
@@ -212,6 +215,8 @@ int make_plan(rtbte_ctx *ctx);
 int launch_prep_from_y(rtbte_ctx *ctx, const double *y, cudaStream_t s);
 int launch_rhs_core(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStream_t s);
 int launch_rows(rtbte_ctx *ctx, unsigned parts, double *out, const double *forcing, cudaStream_t s);
+int split_tables(rtbte_ctx *ctx, int overhead);
+int autotune(rtbte_ctx *ctx, unsigned parts, int *chosen);
 // integrate.cu
 int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *opt, rtbte_stats *st);
 void destroy_graphs(rtbte_ctx *ctx);

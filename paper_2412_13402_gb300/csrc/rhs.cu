@@ -25,7 +25,6 @@ namespace rtbte {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kItemOverhead = 24;  // scheduling weight of an item beyond its entries
 
 template <class R> __device__ __forceinline__ R Fem(R f, R fp, R N) { return f * (R(1) - fp) + N * (f - fp); }
 template <class R> __device__ __forceinline__ R Fab(R f, R fp, R N) { return N * (f - fp) - fp * (R(1) - f); }
@@ -55,26 +54,11 @@ template <class R> __device__ __forceinline__ void warp_reduce2(R &s, R &c) {
     }
 }
 
-template <class R> struct W4;
-template <> struct W4<float> {
-    static __device__ __forceinline__ void load(const void *W, long long v, float w[4]) {
-        float4 x = __ldcs(reinterpret_cast<const float4 *>(W) + v);
-        w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
-    }
-};
-template <> struct W4<double> {
-    static __device__ __forceinline__ void load(const void *W, long long v, double w[4]) {
-        double2 a = __ldcs(reinterpret_cast<const double2 *>(W) + 2 * v);
-        double2 b = __ldcs(reinterpret_cast<const double2 *>(W) + 2 * v + 1);
-        w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
-    }
-};
-
 struct KParams {
     const Item *items;
     const Group *groups;
     int n_groups;
-    const int *cta_v;  // [grid+1] virtual item starts for this part mask
+    const int *warp_v;  // [grid][nwarps+1] virtual item starts of each warp for this part mask
     int rv[3], ri[3], rlen[3];
     int nranges;
     void *partials;
@@ -92,73 +76,158 @@ __device__ __forceinline__ void stage_copy(R *dst, const R *src, int n) {
     }
 }
 
-template <class R, bool STAGED>
-__device__ __forceinline__ void run_item(const KParams &P, const Group &G, int iid, const R *s0, const R *s1, int lane) {
-    const Item it = P.items[iid];
-    const int nv = it.len >> 2;
-    const uint4 *ip = reinterpret_cast<const uint4 *>(G.idx + it.begin);
-    const long long wv0 = it.begin >> 2;
+// Fields of a group that the item loop needs, held in registers.
+template <class R> struct GroupView {
+    const uint32_t *idx;
+    const R *W;
+    const R *s0, *s1;  // staged (or global) populations: e-ph f & N of one mode, ph-e f, ph-ph N
+    const R *Nglob;    // instance phonon populations (ph-e destinations)
+    int part, sb, pb;
+};
+
+// Entry loads of one item: 4 vectors of 4 entries per lane (16-byte streaming loads).
+template <class R> struct Batch;
+template <> struct Batch<float> {
     uint4 iv[4];
-    R wv[4][4];
+    float4 wv[4];
+    __device__ __forceinline__ void issue(const GroupView<float> &V, const Item &it, int lane) {
+        const int nv = it.len >> 2;
+        const uint4 *ip = reinterpret_cast<const uint4 *>(V.idx + it.begin);
+        const float4 *wp = reinterpret_cast<const float4 *>(V.W + it.begin);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int v = lane + 32 * j;
-        if (v < nv) {
-            iv[j] = __ldcs(ip + v);
-            W4<R>::load(G.W, wv0 + v, wv[j]);
+        for (int j = 0; j < 4; ++j) {
+            const int v = lane + 32 * j;
+            if (v < nv) {
+                iv[j] = __ldcs(ip + v);
+                wv[j] = __ldcs(wp + v);
+            }
         }
     }
-    R acc = R(0), cmp = R(0);
-    if (G.part == PART_EPH) {
-        const unsigned smask = (1u << G.s_bits) - 1u;
-        const R fd = s0[it.dest];
-        // s0 = f of the instance, s1 = N of this mode
+    __device__ __forceinline__ float w(int j, int k) const {
+        return k == 0 ? wv[j].x : k == 1 ? wv[j].y : k == 2 ? wv[j].z : wv[j].w;
+    }
+};
+template <> struct Batch<double> {
+    uint4 iv[4];
+    double2 wa[4], wb[4];
+    __device__ __forceinline__ void issue(const GroupView<double> &V, const Item &it, int lane) {
+        const int nv = it.len >> 2;
+        const uint4 *ip = reinterpret_cast<const uint4 *>(V.idx + it.begin);
+        const double2 *wp = reinterpret_cast<const double2 *>(V.W + it.begin);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (lane + 32 * j < nv) {
-                const unsigned e[4] = {iv[j].x, iv[j].y, iv[j].z, iv[j].w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const R fs = s0[e[k] & smask];
-                    const R N = s1[e[k] >> G.s_bits];
-                    const R F = it.proc ? Fab(fd, fs, N) : Fem(fd, fs, N);
-                    two_sum(acc, cmp, wv[j][k] * F);
-                }
+            const int v = lane + 32 * j;
+            if (v < nv) {
+                iv[j] = __ldcs(ip + v);
+                wa[j] = __ldcs(wp + 2 * v);
+                wb[j] = __ldcs(wp + 2 * v + 1);
             }
         }
-    } else if (G.part == PART_PHE) {
-        const unsigned smask = (1u << G.s_bits) - 1u;
-        const R Np = reinterpret_cast<const R *>(P.popN)[G.N_inst + it.dest];
+    }
+    __device__ __forceinline__ double w(int j, int k) const {
+        return k == 0 ? wa[j].x : k == 1 ? wa[j].y : k == 2 ? wb[j].x : wb[j].y;
+    }
+};
+
+__device__ __forceinline__ unsigned comp4(const uint4 &e, int k) {
+    return k == 0 ? e.x : k == 1 ? e.y : k == 2 ? e.z : e.w;
+}
+
+// Sum of W*F over one item: each 4-entry vector is summed with an FMA chain and the vector
+// sums are added with two-sum; the warp then reduces (hi, lo) with compensation.
+template <class R>
+__device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &it, const Batch<R> &b, int lane,
+                                             R &acc, R &cmp) {
+    const int nv = it.len >> 2;
+    acc = R(0);
+    cmp = R(0);
+    if (V.part == PART_EPH) {
+        const unsigned smask = (1u << V.sb) - 1u;
+        const R fd = V.s0[it.dest];
+        if (it.proc == 0) {  // F_em = f(1-f') + N(f-f') = fma(N, f-f', fma(f', -f, f))
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (lane + 32 * j < nv) {
-                const unsigned e[4] = {iv[j].x, iv[j].y, iv[j].z, iv[j].w};
+            for (int j = 0; j < 4; ++j) {
+                if (lane + 32 * j >= nv) continue;
+                R t = R(0);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const R fd = s0[e[k] & smask];
-                    const R fs = s0[e[k] >> G.s_bits];
-                    two_sum(acc, cmp, wv[j][k] * Fab(fd, fs, Np));
+                    const unsigned e = comp4(b.iv[j], k);
+                    const R fs = V.s0[e & smask], N = V.s1[e >> V.sb];
+                    const R F = fma(N, fd - fs, fma(fs, -fd, fd));
+                    t = fma(b.w(j, k), F, t);
                 }
+                two_sum(acc, cmp, t);
             }
+        } else {  // F_abs = N(f-f') - f'(1-f)
+            const R u = R(1) - fd;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (lane + 32 * j >= nv) continue;
+                R t = R(0);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const unsigned e = comp4(b.iv[j], k);
+                    const R fs = V.s0[e & smask], N = V.s1[e >> V.sb];
+                    const R F = fma(N, fd - fs, -fs * u);
+                    t = fma(b.w(j, k), F, t);
+                }
+                two_sum(acc, cmp, t);
+            }
+        }
+    } else if (V.part == PART_PHE) {  // F_abs(f_d, f_s, N_p) with N_p per item
+        const unsigned smask = (1u << V.sb) - 1u;
+        const R Np = V.Nglob[it.dest];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (lane + 32 * j >= nv) continue;
+            R t = R(0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const unsigned e = comp4(b.iv[j], k);
+                const R fd = V.s0[e & smask], fs = V.s0[e >> V.sb];
+                const R F = fma(Np, fd - fs, -fs * (R(1) - fd));
+                t = fma(b.w(j, k), F, t);
+            }
+            two_sum(acc, cmp, t);
         }
     } else {
-        const unsigned pmask = (1u << G.pp_bits) - 1u;
-        const R Na = s0[it.dest];
+        const unsigned pmask = (1u << V.pb) - 1u;
+        const R Na = V.s0[it.dest];
+        if (it.proc == 0) {  // G_em = N(N'+N''+1) - N'N''
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (lane + 32 * j < nv) {
-                const unsigned e[4] = {iv[j].x, iv[j].y, iv[j].z, iv[j].w};
+            for (int j = 0; j < 4; ++j) {
+                if (lane + 32 * j >= nv) continue;
+                R t = R(0);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const R Nb = s0[e[k] & pmask];
-                    const R Nc = s0[e[k] >> G.pp_bits];
-                    const R Gv = it.proc ? Gab(Na, Nb, Nc) : Gem(Na, Nb, Nc);
-                    two_sum(acc, cmp, wv[j][k] * Gv);
+                    const unsigned e = comp4(b.iv[j], k);
+                    const R Nb = V.s0[e & pmask], Nc = V.s0[e >> V.pb];
+                    const R G = fma(-Nb, Nc, fma(Na, Nb + Nc, Na));
+                    t = fma(b.w(j, k), G, t);
                 }
+                two_sum(acc, cmp, t);
+            }
+        } else {  // G_abs = N(N''-N') - N'(N''+1)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (lane + 32 * j >= nv) continue;
+                R t = R(0);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const unsigned e = comp4(b.iv[j], k);
+                    const R Nb = V.s0[e & pmask], Nc = V.s0[e >> V.pb];
+                    const R G = fma(Na, Nc - Nb, -Nb * (Nc + R(1)));
+                    t = fma(b.w(j, k), G, t);
+                }
+                two_sum(acc, cmp, t);
             }
         }
     }
     warp_reduce2(acc, cmp);
+}
+
+template <class R>
+__device__ __forceinline__ void store_partial(const KParams &P, int iid, R acc, R cmp, int lane) {
     if (lane == 0) {
         R *out = reinterpret_cast<R *>(P.partials) + 2LL * iid;
         out[0] = acc;
@@ -166,44 +235,142 @@ __device__ __forceinline__ void run_item(const KParams &P, const Group &G, int i
     }
 }
 
-template <class R, bool STAGED, int MINB>
+__device__ __forceinline__ Item item_from(const int4 &d) {
+    Item it;
+    it.begin = ((long long)(unsigned)d.y << 32) | (unsigned)d.x;
+    it.dest = d.z;
+    it.len = (unsigned short)(d.w & 0xffff);
+    it.proc = (unsigned char)((d.w >> 16) & 0xff);
+    it.pad = 0;
+    return it;
+}
+
+// Item descriptors of a warp's strided sequence are fetched 32 at a time (one per lane) and
+// broadcast with shuffles.
+struct DescStream {
+    const int4 *items;
+    int k0, end, stride;  // first item of the current block, end of the range, item stride
+    int4 cur, nxt;        // this lane's descriptor in the current / next block
+    __device__ __forceinline__ int4 fetch(int base, int lane) const {
+        const int k = base + lane * stride;
+        return k < end ? __ldg(items + k) : make_int4(0, 0, 0, 0);
+    }
+    __device__ __forceinline__ void init(const Item *it, int a, int b, int st, int lane) {
+        items = reinterpret_cast<const int4 *>(it);
+        k0 = a;
+        end = b;
+        stride = st;
+        cur = fetch(a, lane);
+        nxt = fetch(a + 32 * st, lane);
+    }
+    __device__ __forceinline__ Item get(int k, int lane) {  // k advances by `stride` per call
+        if (k - k0 >= 32 * stride) {
+            k0 += 32 * stride;
+            cur = nxt;
+            nxt = fetch(k0 + 32 * stride, lane);
+        }
+        const int src = (k - k0) / stride;
+        int4 d;
+        d.x = __shfl_sync(kFull, cur.x, src);
+        d.y = __shfl_sync(kFull, cur.y, src);
+        d.z = __shfl_sync(kFull, cur.z, src);
+        d.w = __shfl_sync(kFull, cur.w, src);
+        return item_from(d);
+    }
+};
+
+// Items a, a+st, a+2st, ... < b of one group for one warp.  With PIPE, the next item's entry
+// loads are in flight while the current item is computed (two register buffers).
+template <class R, bool PIPE>
+__device__ __forceinline__ void run_range(const KParams &P, const GroupView<R> &V, int a, int b, int st, int lane) {
+    if (a >= b) return;
+    DescStream D;
+    D.init(P.items, a, b, st, lane);
+    R acc, cmp;
+    if (!PIPE) {
+        for (int k = a; k < b; k += st) {
+            const Item it = D.get(k, lane);
+            Batch<R> B;
+            B.issue(V, it, lane);
+            compute_item(V, it, B, lane, acc, cmp);
+            store_partial(P, k, acc, cmp, lane);
+        }
+        return;
+    }
+    Batch<R> A, B;
+    int k = a;
+    Item ia = D.get(k, lane);
+    A.issue(V, ia, lane);
+    for (;;) {
+        const bool hb = k + st < b;
+        Item ib;
+        if (hb) {
+            ib = D.get(k + st, lane);
+            B.issue(V, ib, lane);
+        }
+        compute_item(V, ia, A, lane, acc, cmp);
+        store_partial(P, k, acc, cmp, lane);
+        if (!hb) break;
+        k += st;
+        const bool ha = k + st < b;
+        if (ha) {
+            ia = D.get(k + st, lane);
+            A.issue(V, ia, lane);
+        }
+        compute_item(V, ib, B, lane, acc, cmp);
+        store_partial(P, k, acc, cmp, lane);
+        if (!ha) break;
+        k += st;
+    }
+}
+
+template <class R, bool STAGED, bool PIPE, int MINB>
 __global__ void __launch_bounds__(kRhsThreads, MINB) rhs_kernel(KParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (P.ctl && P.ctl->done) return;
     R *sm = reinterpret_cast<R *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int v0 = P.cta_v[blockIdx.x], v1 = P.cta_v[blockIdx.x + 1];
+    const int *wv = P.warp_v + (long long)blockIdx.x * (nwarps + 1);
+    const int c0 = wv[0], c1 = wv[nwarps];  // this CTA's virtual range
     for (int r = 0; r < P.nranges; ++r) {
-        const int a = max(v0, P.rv[r]), b = min(v1, P.rv[r] + P.rlen[r]);
+        const int a = max(c0, P.rv[r]), b = min(c1, P.rv[r] + P.rlen[r]);
         if (a >= b) continue;
-        const int ra = P.ri[r] + (a - P.rv[r]), rb = ra + (b - a);
+        const int shift = P.ri[r] - P.rv[r];
+        const int ra = a + shift, rb = b + shift;
         int lo = 0, hi = P.n_groups - 1;  // last group with item_begin <= ra
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
             if (P.groups[mid].item_begin <= ra) lo = mid; else hi = mid - 1;
         }
         for (int g = lo; g < P.n_groups; ++g) {
-            const Group G = P.groups[g];
-            if (G.item_begin >= rb) break;
-            const int ia = max(ra, G.item_begin), ib = min(rb, G.item_end);
-            if (ia >= ib) continue;
-            const R *s0, *s1;
+            const Group &G = P.groups[g];
+            const int gb = G.item_begin, ge = G.item_end;
+            if (gb >= rb) break;
+            if (max(ra, gb) >= min(rb, ge)) continue;
+            GroupView<R> V;
+            V.idx = G.idx;
+            V.W = reinterpret_cast<const R *>(G.W);
+            V.part = G.part;
+            V.sb = G.s_bits;
+            V.pb = G.pp_bits;
+            V.Nglob = reinterpret_cast<const R *>(P.popN) + G.N_inst;
+            const R *src0 = reinterpret_cast<const R *>(G.part == PART_PP ? P.popP : P.popf) + G.stage0_src;
+            const R *src1 = reinterpret_cast<const R *>(P.popN) + G.stage1_src;
             if (STAGED) {
+                const int l0 = G.stage0_len, l1 = G.stage1_len;
                 __syncthreads();  // the previous group's readers are done with the buffer
-                const R *src0 = reinterpret_cast<const R *>(G.part == PART_PP ? P.popP : P.popf) + G.stage0_src;
-                stage_copy<R>(sm, src0, G.stage0_len);
-                if (G.stage1_len > 0)
-                    stage_copy<R>(sm + G.stage0_len, reinterpret_cast<const R *>(P.popN) + G.stage1_src, G.stage1_len);
+                stage_copy<R>(sm, src0, l0);
+                if (l1 > 0) stage_copy<R>(sm + l0, src1, l1);
                 asm volatile("cp.async.commit_group;\n" ::: "memory");
                 asm volatile("cp.async.wait_group 0;\n" ::: "memory");
                 __syncthreads();
-                s0 = sm;
-                s1 = sm + G.stage0_len;
+                V.s0 = sm;
+                V.s1 = sm + l0;
             } else {
-                s0 = reinterpret_cast<const R *>(G.part == PART_PP ? P.popP : P.popf) + G.stage0_src;
-                s1 = reinterpret_cast<const R *>(P.popN) + G.stage1_src;
+                V.s0 = src0;
+                V.s1 = src1;
             }
-            for (int iid = ia + warp; iid < ib; iid += nwarps) run_item<R, STAGED>(P, G, iid, s0, s1, lane);
+            run_range<R, PIPE>(P, V, max(ra, gb) + warp, min(rb, ge), nwarps, lane);
         }
     }
 }
@@ -253,6 +420,45 @@ RowParams row_params(rtbte_ctx *ctx) {
     Q.popN = ctx->popN.p;
     Q.popP = ctx->popP.p;
     return Q;
+}
+
+// Per-mask work split of the persistent grid: CTA c owns the virtual items [t[c], t[c+1]) of
+// equal weight, weight = entries + `overhead` per item (the fixed cost of an item in entry
+// equivalents); stored as [grid][nwarps+1] virtual starts (warp columns split the CTA range
+// by the same weights).
+int split_tables(rtbte_ctx *ctx, int overhead) {
+    const int G = ctx->grid;
+    const int NW = kRhsThreads / 32;
+    const std::vector<unsigned short> &len = ctx->item_len_h;
+    std::vector<int> tab(7LL * G * (NW + 1), 0);
+    std::vector<long long> vpre;
+    for (unsigned mask = 1; mask <= 7; ++mask) {
+        vpre.assign(1, 0);
+        for (int part = 0; part < 3; ++part) {
+            if (!(mask & (1u << part))) continue;
+            const long long sc = (long long)(64.0 * ctx->part_scale[part] + 0.5);  // cost per entry-equivalent
+            for (int k = ctx->part_first[part]; k < ctx->part_first[part] + ctx->part_items[part]; ++k)
+                vpre.push_back(vpre.back() + sc * (len[k] + overhead));
+        }
+        const long long total = vpre.back();
+        const int nv = (int)vpre.size() - 1;
+        auto at = [&](long long target) {
+            int k = (int)(std::lower_bound(vpre.begin(), vpre.end(), target) - vpre.begin());
+            return std::min(k, nv);
+        };
+        int *t = tab.data() + (long long)(mask - 1) * G * (NW + 1);
+        for (int c = 0; c < G; ++c) {
+            const long long c0 = total * c / G, c1 = total * (c + 1) / G;
+            const int v0 = c == 0 ? 0 : at(c0), v1 = c == G - 1 ? nv : at(c1);
+            const long long w0 = vpre[v0], w1 = vpre[v1];
+            int *row = t + (long long)c * (NW + 1);
+            row[0] = v0;
+            row[NW] = v1;
+            for (int w = 1; w < NW; ++w) row[w] = std::max(v0, std::min(v1, at(w0 + (w1 - w0) * w / NW)));
+        }
+    }
+    ctx->item_overhead = overhead;
+    return upload_vec(ctx, ctx->cta_tab, tab);
 }
 
 // Build the work items, staging groups, per-row item offsets and per-CTA work ranges.
@@ -393,30 +599,8 @@ int make_plan(rtbte_ctx *ctx) {
     ctx->staged = max_stage <= ctx->smem_optin;
     ctx->smem_bytes = ctx->staged ? std::max<size_t>(max_stage, 16) : 0;
     ctx->grid = ctx->num_sms * (ctx->staged ? 1 : 2);
-    // per-mask CTA work ranges over the virtual item list of the enabled parts
-    const int G = ctx->grid;
-    std::vector<long long> wpre(items.size() + 1, 0);
-    for (size_t k = 0; k < items.size(); ++k) wpre[k + 1] = wpre[k] + items[k].len + kItemOverhead;
-    std::vector<int> tab(7 * (G + 1), 0);
-    std::vector<long long> vpre;
-    for (unsigned mask = 1; mask <= 7; ++mask) {
-        vpre.assign(1, 0);
-        for (int part = 0; part < 3; ++part) {
-            if (!(mask & (1u << part))) continue;
-            for (int k = ctx->part_first[part]; k < ctx->part_first[part] + ctx->part_items[part]; ++k)
-                vpre.push_back(vpre.back() + items[k].len + kItemOverhead);
-        }
-        const long long total = vpre.back();
-        const int nv = (int)vpre.size() - 1;
-        int *t = tab.data() + (mask - 1) * (G + 1);
-        for (int c = 0; c <= G; ++c) {
-            long long target = total * c / G;
-            int k = (int)(std::lower_bound(vpre.begin(), vpre.end(), target) - vpre.begin());
-            t[c] = std::min(k, nv);
-        }
-        t[0] = 0;
-        t[G] = nv;
-    }
+    ctx->item_len_h.resize(items.size());
+    for (size_t k = 0; k < items.size(); ++k) ctx->item_len_h[k] = items[k].len;
     int rc;
     if ((rc = upload_vec(ctx, ctx->items, items))) return rc;
     if ((rc = upload_vec(ctx, ctx->groups, groups))) return rc;
@@ -425,7 +609,7 @@ int make_plan(rtbte_ctx *ctx) {
     if ((rc = upload_vec(ctx, ctx->ppoff, ppoff))) return rc;
     if ((rc = upload_vec(ctx, ctx->instdev, idev))) return rc;
     if ((rc = upload_vec(ctx, ctx->compact, compact))) return rc;
-    if ((rc = upload_vec(ctx, ctx->cta_tab, tab))) return rc;
+    if ((rc = split_tables(ctx, ctx->item_overhead))) return rc;
     ctx->partials.release();
     size_t pb = std::max<size_t>(2 * R * (size_t)std::max(ctx->n_items, 1), 16);
     RT_CUDA(ctx, cudaMalloc(&ctx->partials.p, pb));
@@ -434,10 +618,10 @@ int make_plan(rtbte_ctx *ctx) {
     RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (ctx->staged) {
         if (ctx->precision == RTBTE_PREC_FP64)
-            RT_CUDA(ctx, cudaFuncSetAttribute(rhs_kernel<double, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            RT_CUDA(ctx, cudaFuncSetAttribute(rhs_kernel<double, true, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)ctx->smem_bytes));
         else
-            RT_CUDA(ctx, cudaFuncSetAttribute(rhs_kernel<float, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            RT_CUDA(ctx, cudaFuncSetAttribute(rhs_kernel<float, true, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)ctx->smem_bytes));
     }
     ctx->plan_valid = true;
@@ -464,7 +648,7 @@ static int launch_core_t(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStr
     P.items = ctx->items.as<Item>();
     P.groups = ctx->groups.as<Group>();
     P.n_groups = ctx->n_groups;
-    P.cta_v = ctx->cta_tab.as<int>() + (parts - 1) * (ctx->grid + 1);
+    P.warp_v = ctx->cta_tab.as<int>() + (long long)(parts - 1) * ctx->grid * (kRhsThreads / 32 + 1);
     int v = 0;
     for (int part = 0; part < 3; ++part)
         if (parts & (1u << part)) {
@@ -497,9 +681,9 @@ static int launch_core_t(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStr
         }
     }
     if (ctx->staged) {
-        rhs_kernel<R, true, 1><<<ctx->grid, ctx->threads, ctx->smem_bytes, s>>>(P);
+        rhs_kernel<R, true, sizeof(R) == 4, 1><<<ctx->grid, ctx->threads, ctx->smem_bytes, s>>>(P);
     } else {
-        rhs_kernel<R, false, 2><<<ctx->grid, ctx->threads, 0, s>>>(P);
+        rhs_kernel<R, false, false, 2><<<ctx->grid, ctx->threads, 0, s>>>(P);
     }
     RT_CUDA(ctx, cudaGetLastError());
     ctx->launches++;
@@ -514,6 +698,90 @@ int launch_rhs_core(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStream_t
     if (parts == 0 || parts > 7) return fail(ctx, RTBTE_E_INVALID_ARG, "parts must be a non-empty subset of RTBTE_ALL");
     return ctx->precision == RTBTE_PREC_FP64 ? launch_core_t<double>(ctx, parts, ctl, s)
                                              : launch_core_t<float>(ctx, parts, ctl, s);
+}
+
+// Autotuner of the work split: time the collision kernel with each candidate per-item weight
+// and keep the fastest.
+int autotune(rtbte_ctx *ctx, unsigned parts, int *chosen) {
+    static const int cand[] = {32, 96, 192, 320, 512, 800, 1280, 2048};
+    cudaEvent_t e0, e1;
+    RT_CUDA(ctx, cudaEventCreate(&e0));
+    RT_CUDA(ctx, cudaEventCreate(&e1));
+    int best = ctx->item_overhead, rc = RTBTE_OK;
+    float best_ms = 1e30f;
+    for (int w : cand) {
+        if ((rc = split_tables(ctx, w))) break;
+        if ((rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) break;
+        RT_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+        for (int r = 0; r < 3 && !rc; ++r) rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream);
+        if (rc) break;
+        RT_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+        RT_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        RT_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = w;
+        }
+    }
+    if (rc) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+    }
+    if ((rc = split_tables(ctx, best))) return rc;
+    // calibrate the relative cost of an entry in each part from single-part launches, keep it
+    // if the combined launch gets faster
+    const double scale0[3] = {ctx->part_scale[0], ctx->part_scale[1], ctx->part_scale[2]};
+    double t[3] = {0, 0, 0}, wsum[3] = {0, 0, 0};
+    int used = 0;
+    for (int part = 0; part < 3 && !rc; ++part) {
+        if (!(parts & (1u << part)) || ctx->part_items[part] == 0) continue;
+        for (int k = ctx->part_first[part]; k < ctx->part_first[part] + ctx->part_items[part]; ++k)
+            wsum[part] += ctx->item_len_h[k] + best;
+        const unsigned pm = 1u << part;
+        if ((rc = launch_rhs_core(ctx, pm, nullptr, ctx->stream))) break;
+        RT_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+        for (int r = 0; r < 3 && !rc; ++r) rc = launch_rhs_core(ctx, pm, nullptr, ctx->stream);
+        if (rc) break;
+        RT_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+        RT_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        RT_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        t[part] = ms;
+        used |= pm;
+    }
+    if (!rc && used) {
+        double ref = 0.0;
+        int nref = 0;
+        for (int part = 0; part < 3; ++part)
+            if (used & (1u << part)) {
+                ref += t[part] / wsum[part];
+                ++nref;
+            }
+        ref /= nref;
+        for (int part = 0; part < 3; ++part)
+            if (used & (1u << part)) ctx->part_scale[part] = (t[part] / wsum[part]) / ref;
+        if (!(rc = split_tables(ctx, best))) {
+            float ms = 0.f;
+            if (!(rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) {
+                RT_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+                for (int r = 0; r < 3 && !rc; ++r) rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream);
+                RT_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+                RT_CUDA(ctx, cudaEventSynchronize(e1));
+                RT_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+            }
+            if (!rc && ms > best_ms) {  // calibration did not help: back to uniform costs
+                for (int part = 0; part < 3; ++part) ctx->part_scale[part] = scale0[part];
+                rc = split_tables(ctx, best);
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (chosen) *chosen = best;
+    return RTBTE_OK;
 }
 
 int launch_rows(rtbte_ctx *ctx, unsigned parts, double *out, const double *forcing, cudaStream_t s) {

@@ -154,6 +154,21 @@ def test_rhs_host_pointers_and_determinism(rt):
     ctx.close()
 
 
+def test_autotune_keeps_results_bitwise(rt):
+    m = ri.graphene_small(36)
+    ctx = rt.Context(m)
+    ctx.upload_channels()
+    y = torch.tensor(sym_state(m, 8), device="cuda")
+    before = ctx.rhs(y).cpu().numpy()
+    w = ctx.autotune(ALL)
+    assert w > 0
+    after = ctx.rhs(y).cpu().numpy()
+    assert np.array_equal(before, after)
+    st = ctx.advance_to(0.01, y, method="zon43", t0=0.0)
+    assert st["status"] == 0
+    ctx.close()
+
+
 def test_batched_instances_equal_single_contexts(rt):
     ms = [ri.graphene_small(24), ri.graphene_small(36, seed=5), ri.graphene(n=30, window=0.6, seed=77)]
     ctx = rt.Context(ms)

@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: only standalone full-RHS evaluations (warm-up + steps), no JSON line")
     ap.add_argument("--grid", type=int, default=180, help="k/q grid side of the graphene-like workload (profiling)")
@@ -230,6 +231,55 @@ def traffic_from_profile(kernel_src):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def run_ensemble(args, rt, ri, dev, peak):
+    """64 graphene-like instances (sides 24..96, E_x 0.1-1 eV, T 100-500 K) in one context:
+    adaptive Zonneveld windows with per-instance controllers; throughput in instance-RHS
+    evaluations per second, plus the batched collision kernel's roofline."""
+    import torch
+
+    ms = ri.ensemble()
+    ctx = rt.Context(ms, precision="fp32", device=dev.index or 0)
+    for i in range(len(ms)):
+        ctx.upload_channels(i)
+    entries = sum(ctx.sizes(i)["eph_entries"] + ctx.sizes(i)["phe_entries"] + ctx.sizes(i)["pp_entries"]
+                  for i in range(len(ms)))
+    y = torch.tensor(__import__("numpy").concatenate([m.y0() for m in ms]), device=dev)
+    ctx.rhs(y, torch.empty_like(y))
+    w = ctx.autotune(rt.RTBTE_ALL)
+    t, h0 = 0.0, 0.0
+    for _ in range(args.warmup):
+        st = ctx.advance_to(t + WINDOW_PS, y, method="zon43", t0=t, h0=h0, **TOL)
+        assert st["status"] == 0, st
+        t, h0 = st["t"], st["h_next"]
+    steps = max(4, args.steps // 8)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_rhs = 0
+    e0.record(ctx.stream)
+    for _ in range(steps):
+        st = ctx.advance_to(t + WINDOW_PS, y, method="zon43", t0=t, **TOL)
+        assert st["status"] == 0, st
+        t = st["t"]
+        n_rhs += st["rhs_full"]
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms_t = e0.elapsed_time(e1)
+    ctx.set_kernel_timing(True)
+    yd = torch.empty_like(y)
+    ctx.kernel_time()
+    for _ in range(20):
+        ctx.rhs(y, yd)
+    kms, kn = ctx.kernel_time()
+    ctx.set_kernel_timing(False)
+    ach = 8.0 * entries / (kms / kn / 1000.0) / 1e9
+    ctx.close()
+    return {"instances": len(ms), "sides": [m.nk[0] for m in ms], "state_rows": int(y.numel()),
+            "channel_entries": entries, "steps": steps, "window_fs": WINDOW_PS * 1000,
+            "instance_rhs_evals_per_s": n_rhs / (ms_t / 1000.0), "sim_ps_per_s_per_instance":
+                steps * WINDOW_PS / (ms_t / 1000.0), "ms": ms_t, "autotuned_split_weight": w,
+            "rhs_kernel": {"avg_launch_ms": kms / kn, "achieved_gbs": ach, "frac_of_measured_peak": ach / peak}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -356,6 +406,10 @@ def run_ours(args):
     mri = {"sim_ps_per_s": mri_steps * hs / (mri_ms / 1000.0), "h_s_fs": hs * 1000, "slow_steps": st["slow_steps"],
            "rhs_fast": st["rhs_fast"], "rhs_slow": st["rhs_slow"], "fast_steps": st["steps"], "ms": mri_ms}
 
+    # ---- batched ensemble: 64 independent instances of uneven size, one persistent launch
+    # per RHS, per-instance adaptive controllers
+    ens = run_ensemble(args, rt, ri, dev, peak) if not args.no_ensemble else None
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -374,7 +428,8 @@ def run_ours(args):
                            "channel_entries": entries, "replicas": world, "parallelism": f"replicas x{world}",
                            "autotuned_split_weight": split_weight},
                 "sim_ps_per_s": sim_ps * world / (tmax / 1000.0), "rhs_evals_timed": tot_rhs,
-                "roofline": roofline, "e2e": e2e, "mri": mri, "clocks": clk.summary(), "gpu_launches": launches,
+                "roofline": roofline, "e2e": e2e, "mri": mri, "ensemble": ens, "clocks": clk.summary(),
+                "gpu_launches": launches,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -328,11 +328,12 @@ int rtbte_create(const rtbte_desc *d, rtbte_ctx **out) {
         (rc = dev_alloc(ctx, ctx->K, sizeof(double) * y * kMaxStages, true)) ||
         (rc = dev_alloc(ctx, ctx->Fs, sizeof(double) * y * 3, true)) ||
         (rc = dev_alloc(ctx, ctx->forcing, sizeof(double) * y, true)) ||
-        (rc = dev_alloc(ctx, ctx->wrms_part, sizeof(double) * 2 * kWrmsBlocks, true)) ||
-        (rc = dev_alloc(ctx, ctx->ctl, sizeof(Ctl), true)))
+        (rc = dev_alloc(ctx, ctx->wrms_part, sizeof(double) * 2 * y, true)) ||
+        (rc = dev_alloc(ctx, ctx->ctl, sizeof(Ctl) * d->n_instances, true)))
         return bail(rc);
-    if (cudaMallocHost(&ctx->ctl_host, sizeof(Ctl)) != cudaSuccess) return bail(cuda_fail(ctx, cudaErrorMemoryAllocation, "cudaMallocHost"));
-    std::memset(ctx->ctl_host, 0, sizeof(Ctl));
+    if (cudaMallocHost(&ctx->ctl_host, sizeof(Ctl) * d->n_instances) != cudaSuccess)
+        return bail(cuda_fail(ctx, cudaErrorMemoryAllocation, "cudaMallocHost"));
+    std::memset(ctx->ctl_host, 0, sizeof(Ctl) * d->n_instances);
     for (int i = 0; i < d->n_instances; ++i)
         if ((rc = upload_tables(ctx, i))) return bail(rc);
     *out = ctx;
@@ -491,7 +492,7 @@ void rtbte_destroy(rtbte_ctx *ctx) {
         for (DevBuf *b : bufs) b->release();
     }
     DevBuf *bufs[] = {&ctx->popf, &ctx->popN, &ctx->popP, &ctx->instdev, &ctx->compact, &ctx->items, &ctx->groups,
-                      &ctx->partials, &ctx->eoff, &ctx->poff, &ctx->ppoff, &ctx->cta_tab, &ctx->Y[0], &ctx->Y[1],
+                      &ctx->partials, &ctx->eoff, &ctx->poff, &ctx->ppoff, &ctx->cta_tab, &ctx->wpre, &ctx->dyn_tab, &ctx->Y[0], &ctx->Y[1],
                       &ctx->K, &ctx->Fs, &ctx->forcing, &ctx->wrms_part, &ctx->ctl, &ctx->ystage, &ctx->ydstage};
     for (DevBuf *b : bufs) b->release();
     for (auto &pr : ctx->ev_pending) {

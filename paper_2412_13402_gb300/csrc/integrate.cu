@@ -85,48 +85,35 @@ Mis mis_kw3() {
 struct StageArgs {
     Tableau T;
     CtlParams cp;
-    Ctl *ctl;
+    Ctl *ctl;  // one controller per instance
     double *Y0, *Y1, *K;
     const double *forcing;
-    double *wrms_part;
+    double *wsq;  // per-row squared weighted error of the last stage
     long long n;
     unsigned parts;
     int stage;         // -1: populations <- y; 0..S-1: combine stage `stage`
-    int respect_done;  // inside an attempt sequence: skip once the integration is done
+    int respect_done;  // inside an attempt sequence: skip instances whose integration is done
 };
 
 __device__ __forceinline__ double atol_of(const CtlParams &cp, const InstDev &I, long long local) {
     return local < I.n_c ? cp.atol_c : cp.atol_ph;
 }
 
-__device__ __forceinline__ void block_sum_store(double v, double *dst) {
-    __shared__ double red[kRedThreads];
-    red[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *dst = red[0];
-}
-
 template <class R>
 __global__ void __launch_bounds__(kRedThreads) stage_kernel(RowParams Q, StageArgs a) {
-    const Ctl *ctl = a.ctl;
-    if (a.respect_done && ctl->done) return;
-    const double *y = ctl->cur ? a.Y1 : a.Y0;
-    double *yn = ctl->cur ? a.Y0 : a.Y1;
-    const double h = ctl->h_try;
     const int S = a.T.S, i = a.stage;
-    double wsum = 0.0;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.n; c += (long long)gridDim.x * blockDim.x) {
         const int ii = Q.n_inst > 1 ? find_inst(Q, c) : 0;
+        const Ctl *C = a.ctl + ii;
+        if (a.respect_done && C->done) continue;
         const InstDev I = Q.inst[ii];
         const long long local = c - I.y_off;
+        const double *y = C->cur ? a.Y1 : a.Y0;
         if (i < 0) {
             write_pops<R>(Q, I, local, y[c]);
             continue;
         }
+        const double h = C->h_try;
         double k = row_value<R>(Q, I, local, a.parts);
         if (a.forcing) k += a.forcing[c];
         a.K[(long long)i * a.n + c] = k;
@@ -142,30 +129,32 @@ __global__ void __launch_bounds__(kRedThreads) stage_kernel(RowParams Q, StageAr
                 s2 += (a.T.b[j] - a.T.bt[j]) * kj;
             }
             const double ynew = y[c] + h * s1;
-            yn[c] = ynew;
+            (C->cur ? a.Y0 : a.Y1)[c] = ynew;
+            double x2 = 0.0;
             if (a.T.has_emb) {
                 const double e = h * s2;
                 const double w = 1.0 / (a.cp.rtol * fabs(y[c]) + atol_of(a.cp, I, local));
                 const double x = e * w;
-                wsum += x * x;
+                x2 = x * x;
             }
-            if (!isfinite(ynew)) wsum += __longlong_as_double(0x7ff8000000000000LL);
+            if (!isfinite(ynew)) x2 = __longlong_as_double(0x7ff8000000000000LL);
+            a.wsq[c] = x2;
         }
     }
-    if (i == S - 1) block_sum_store(wsum, a.wrms_part + blockIdx.x);
 }
 
-__device__ double reduce_parts(const double *part, int n) {
+// Fixed-order sum of v[b .. b+n) by one block.
+__device__ double block_sum(const double *v, long long b, long long n) {
     __shared__ double red[kRedThreads];
-    double v = 0.0;
-    for (int b = threadIdx.x; b < n; b += blockDim.x) v += part[b];
-    red[threadIdx.x] = v;
+    double acc = 0.0;
+    for (long long r = threadIdx.x; r < n; r += blockDim.x) acc += v[b + r];
+    red[threadIdx.x] = acc;
     __syncthreads();
     for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    double r = red[0];
+    const double r = red[0];
     __syncthreads();
     return r;
 }
@@ -185,11 +174,15 @@ __device__ __forceinline__ void arm(Ctl *c) {
     c->h_try = hk;
 }
 
-__global__ void controller_kernel(Ctl *c, CtlParams cp, const double *part, int nparts, long long n) {
+// One block per instance: WRMS norm (Eq. wrms_norm) of its rows, accept/reject, PID proposal.
+__global__ void controller_kernel(RowParams Q, Ctl *ctl, CtlParams cp, const double *wsq) {
+    Ctl *c = ctl + blockIdx.x;
     if (c->done) return;
-    const double sum = reduce_parts(part, nparts);
+    const InstDev I = Q.inst[blockIdx.x];
+    const long long ni = (long long)I.n_c + I.n_ph;
+    const double sum = block_sum(wsq, I.y_off, ni);
     if (threadIdx.x != 0) return;
-    const double eps = sqrt(sum / (double)n);
+    const double eps = sqrt(sum / (double)ni);
     c->attempts++;
     if (!isfinite(eps)) {
         c->status = RTBTE_E_NONFINITE;
@@ -263,35 +256,34 @@ __global__ void controller_kernel(Ctl *c, CtlParams cp, const double *part, int 
     arm(c);
 }
 
-// ---- Hairer-Norsett-Wanner starting step ---------------------------------------------
+// ---- Hairer-Norsett-Wanner starting step, per instance --------------------------------
 __global__ void __launch_bounds__(kRedThreads) h0_norms(RowParams Q, CtlParams cp, const Ctl *ctl, const double *Y0,
                                                          const double *Y1, const double *K0, const double *K1,
-                                                         double *part, int second, long long n) {
-    const double *y = ctl->cur ? Y1 : Y0;
-    double s0 = 0.0, s1 = 0.0;
+                                                         double *wsq, int second, long long n) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int ii = Q.n_inst > 1 ? find_inst(Q, c) : 0;
         const InstDev I = Q.inst[ii];
+        const double *y = ctl[ii].cur ? Y1 : Y0;
         const double w = 1.0 / (cp.rtol * fabs(y[c]) + atol_of(cp, I, c - I.y_off));
         if (!second) {
             const double a = y[c] * w, b = K0[c] * w;
-            s0 += a * a;
-            s1 += b * b;
+            wsq[c] = a * a;
+            wsq[n + c] = b * b;
         } else {
             const double d = (K1[c] - K0[c]) * w;
-            s0 += d * d;
+            wsq[c] = d * d;
         }
     }
-    block_sum_store(s0, part + blockIdx.x);
-    __syncthreads();
-    if (!second) block_sum_store(s1, part + gridDim.x + blockIdx.x);
 }
 
-__global__ void h0_first(Ctl *c, const double *part, int nparts, long long n, double span) {
-    const double s0 = reduce_parts(part, nparts);
-    const double s1 = reduce_parts(part + nparts, nparts);
+__global__ void h0_first(RowParams Q, Ctl *ctl, const double *wsq, long long n, double span) {
+    Ctl *c = ctl + blockIdx.x;
+    const InstDev I = Q.inst[blockIdx.x];
+    const long long ni = (long long)I.n_c + I.n_ph;
+    const double s0 = block_sum(wsq, I.y_off, ni);
+    const double s1 = block_sum(wsq + n, I.y_off, ni);
     if (threadIdx.x != 0) return;
-    const double d0 = sqrt(s0 / (double)n), d1 = sqrt(s1 / (double)n);
+    const double d0 = sqrt(s0 / (double)ni), d1 = sqrt(s1 / (double)ni);
     double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
     if (h0 > span) h0 = span;
     c->h0tmp = h0;
@@ -300,20 +292,22 @@ __global__ void h0_first(Ctl *c, const double *part, int nparts, long long n, do
 
 template <class R>
 __global__ void h0_probe(RowParams Q, const Ctl *ctl, const double *Y0, const double *Y1, const double *K0, long long n) {
-    const double *y = ctl->cur ? Y1 : Y0;
-    const double h0 = ctl->h0tmp;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int ii = Q.n_inst > 1 ? find_inst(Q, c) : 0;
         const InstDev I = Q.inst[ii];
-        write_pops<R>(Q, I, c - I.y_off, y[c] + h0 * K0[c]);
+        const double *y = ctl[ii].cur ? Y1 : Y0;
+        write_pops<R>(Q, I, c - I.y_off, y[c] + ctl[ii].h0tmp * K0[c]);
     }
 }
 
-__global__ void h0_second(Ctl *c, CtlParams cp, const double *part, int nparts, long long n, double span) {
-    const double s = reduce_parts(part, nparts);
+__global__ void h0_second(RowParams Q, Ctl *ctl, CtlParams cp, const double *wsq, double span) {
+    Ctl *c = ctl + blockIdx.x;
+    const InstDev I = Q.inst[blockIdx.x];
+    const long long ni = (long long)I.n_c + I.n_ph;
+    const double s = block_sum(wsq, I.y_off, ni);
     if (threadIdx.x != 0) return;
     const double h0 = c->h0tmp, d1 = c->eps;
-    const double d2 = sqrt(s / (double)n) / h0;
+    const double d2 = sqrt(s / (double)ni) / h0;
     const double dm = d1 > d2 ? d1 : d2;
     const double h1 = dm <= 1e-15 ? fmax(1e-6, h0 * 1e-3) : pow(0.01 / dm, 1.0 / (cp.p + 1));
     double h = 100.0 * h0 < h1 ? 100.0 * h0 : h1;
@@ -324,10 +318,16 @@ __global__ void h0_second(Ctl *c, CtlParams cp, const double *part, int nparts, 
     arm(c);
 }
 
-__global__ void arm_kernel(Ctl *c) { arm(c); }
+__global__ void arm_kernel(Ctl *ctl, int n_inst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_inst) arm(ctl + i);
+}
 
 // Inner (fast) ERK restart for an MRI stage: fresh error history, carried step proposal.
-__global__ void mri_stage_reset(Ctl *c, CtlParams cp, double ta, double tb) {
+__global__ void mri_stage_reset(Ctl *ctl, int n_inst, CtlParams cp, double ta, double tb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inst) return;
+    Ctl *c = ctl + i;
     c->t = ta;
     c->t_out = tb;
     c->eps1 = 1.0;
@@ -357,6 +357,7 @@ __global__ void mri_forcing(double *r, const double *Fs, double om0, double om1,
 
 // ---- host helpers -----------------------------------------------------------------------
 int row_grid(rtbte_ctx *ctx) { return (int)std::min<long long>((ctx->n_y + kRedThreads - 1) / kRedThreads, kWrmsBlocks); }
+int n_inst(rtbte_ctx *ctx) { return (int)ctx->inst.size(); }
 
 template <class R>
 int launch_stage(rtbte_ctx *ctx, const StageArgs &a, cudaStream_t s) {
@@ -380,7 +381,7 @@ StageArgs stage_args(rtbte_ctx *ctx, const Tableau &T, const CtlParams &cp, unsi
     a.Y1 = ctx->Y[1].as<double>();
     a.K = ctx->K.as<double>();
     a.forcing = forcing;
-    a.wrms_part = ctx->wrms_part.as<double>();
+    a.wsq = ctx->wrms_part.as<double>();
     a.n = ctx->n_y;
     a.parts = parts;
     return a;
@@ -399,8 +400,8 @@ int enqueue_attempt(rtbte_ctx *ctx, const Tableau &T, const CtlParams &cp, unsig
         a.stage = i;
         if ((rc = stage(ctx, a, s))) return rc;
     }
-    controller_kernel<<<1, kRedThreads, 0, s>>>(ctx->ctl.as<Ctl>(), cp, ctx->wrms_part.as<double>(), row_grid(ctx),
-                                                 ctx->n_y);
+    controller_kernel<<<n_inst(ctx), kRedThreads, 0, s>>>(row_params(ctx), ctx->ctl.as<Ctl>(), cp,
+                                                          ctx->wrms_part.as<double>());
     RT_CUDA(ctx, cudaGetLastError());
     ctx->launches++;
     return RTBTE_OK;
@@ -418,11 +419,11 @@ long long graph_key(int method, unsigned parts, bool forcing, const CtlParams &c
 int attempt_graph(rtbte_ctx *ctx, int method, const CtlParams &cp, unsigned parts, const double *forcing,
                   cudaGraphExec_t *out, int *nlaunch) {
     const Tableau T = tableau_of(method);
-    *nlaunch = 2 * T.S + 2;
     long long key = graph_key(method, parts, forcing != nullptr, cp);
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
         *out = it->second;
+        *nlaunch = ctx->graph_launches[key];
         return RTBTE_OK;
     }
     cudaGraph_t g;
@@ -430,7 +431,8 @@ int attempt_graph(rtbte_ctx *ctx, int method, const CtlParams &cp, unsigned part
     RT_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = enqueue_attempt(ctx, T, cp, parts, forcing, ctx->cap_stream);
     cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
-    ctx->launches = before;  // captured, not executed
+    ctx->graph_launches[key] = (int)(ctx->launches - before);  // kernels per replay
+    ctx->launches = before;                                   // captured, not executed
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
     cudaGraphExec_t ex;
@@ -439,47 +441,64 @@ int attempt_graph(rtbte_ctx *ctx, int method, const CtlParams &cp, unsigned part
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
     ctx->graphs[key] = ex;
     *out = ex;
+    *nlaunch = ctx->graph_launches[key];
     return RTBTE_OK;
 }
 
 int read_ctl(rtbte_ctx *ctx) {
-    RT_CUDA(ctx, cudaMemcpyAsync(ctx->ctl_host, ctx->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    RT_CUDA(ctx, cudaMemcpyAsync(ctx->ctl_host, ctx->ctl.p, sizeof(Ctl) * n_inst(ctx), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
     RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return RTBTE_OK;
 }
 
 int write_ctl(rtbte_ctx *ctx) {
-    RT_CUDA(ctx, cudaMemcpyAsync(ctx->ctl.p, ctx->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+    RT_CUDA(ctx, cudaMemcpyAsync(ctx->ctl.p, ctx->ctl_host, sizeof(Ctl) * n_inst(ctx), cudaMemcpyHostToDevice,
+                                 ctx->stream));
     RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return RTBTE_OK;
 }
 
-// Run attempts until the device says done.  Returns a CUDA/launch error code, else RTBTE_OK
-// (the integration status is then in ctx->ctl_host->status).
+bool all_done(rtbte_ctx *ctx) {
+    for (int i = 0; i < n_inst(ctx); ++i)
+        if (!ctx->ctl_host[i].done) return false;
+    return true;
+}
+
+long long sum_attempts(rtbte_ctx *ctx) {
+    long long a = 0;
+    for (int i = 0; i < n_inst(ctx); ++i) a += ctx->ctl_host[i].attempts;
+    return a;
+}
+
+// Run attempts until every instance is done.  Returns a CUDA/launch error code, else RTBTE_OK
+// (the integration status of each instance is in ctx->ctl_host[i].status).  *attempts_out
+// receives the instance-attempts performed (one per active instance per attempt).
 int run_attempts(rtbte_ctx *ctx, int method, const CtlParams &cp, unsigned parts, const double *forcing, int chunk,
                  long long *attempts_out) {
     cudaGraphExec_t ex;
     int nl, rc;
     if ((rc = attempt_graph(ctx, method, cp, parts, forcing, &ex, &nl))) return rc;
-    long long a0 = ctx->ctl_host->attempts;
+    long long a0 = sum_attempts(ctx);
     for (;;) {
         for (int k = 0; k < chunk; ++k) {
             RT_CUDA(ctx, cudaGraphLaunch(ex, ctx->stream));
             ctx->launches += nl;
         }
         if ((rc = read_ctl(ctx))) return rc;
-        if (ctx->ctl_host->done) break;
+        if (all_done(ctx)) break;
     }
-    if (attempts_out) *attempts_out = ctx->ctl_host->attempts - a0;
+    if (attempts_out) *attempts_out = sum_attempts(ctx) - a0;
     return RTBTE_OK;
 }
 
-// Hairer-Norsett-Wanner first step; 2 RHS evaluations of `parts` (+ forcing).
+// Hairer-Norsett-Wanner first step for every instance; 2 RHS evaluations of `parts` (+ forcing).
 int h0_estimate(rtbte_ctx *ctx, const CtlParams &cp, unsigned parts, const double *forcing, double span) {
     const int nb = row_grid(ctx);
     RowParams Q = row_params(ctx);
     Ctl *c = ctx->ctl.as<Ctl>();
     double *K0 = ctx->K.as<double>(), *K1 = K0 + ctx->n_y;
+    double *wsq = ctx->wrms_part.as<double>();
     StageArgs a = stage_args(ctx, tableau_of(RTBTE_ZON43), cp, parts, forcing);
     a.stage = -1;
     int rc;
@@ -487,8 +506,8 @@ int h0_estimate(rtbte_ctx *ctx, const CtlParams &cp, unsigned parts, const doubl
     if ((rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) return rc;
     if ((rc = launch_rows(ctx, parts, K0, forcing, ctx->stream))) return rc;
     h0_norms<<<nb, kRedThreads, 0, ctx->stream>>>(Q, cp, c, ctx->Y[0].as<double>(), ctx->Y[1].as<double>(), K0, K1,
-                                                  ctx->wrms_part.as<double>(), 0, ctx->n_y);
-    h0_first<<<1, kRedThreads, 0, ctx->stream>>>(c, ctx->wrms_part.as<double>(), nb, ctx->n_y, span);
+                                                  wsq, 0, ctx->n_y);
+    h0_first<<<n_inst(ctx), kRedThreads, 0, ctx->stream>>>(Q, c, wsq, ctx->n_y, span);
     if (ctx->precision == RTBTE_PREC_FP64)
         h0_probe<double><<<nb, kRedThreads, 0, ctx->stream>>>(Q, c, ctx->Y[0].as<double>(), ctx->Y[1].as<double>(), K0,
                                                               ctx->n_y);
@@ -500,8 +519,8 @@ int h0_estimate(rtbte_ctx *ctx, const CtlParams &cp, unsigned parts, const doubl
     if ((rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) return rc;
     if ((rc = launch_rows(ctx, parts, K1, forcing, ctx->stream))) return rc;
     h0_norms<<<nb, kRedThreads, 0, ctx->stream>>>(Q, cp, c, ctx->Y[0].as<double>(), ctx->Y[1].as<double>(), K0, K1,
-                                                  ctx->wrms_part.as<double>(), 1, ctx->n_y);
-    h0_second<<<1, kRedThreads, 0, ctx->stream>>>(c, cp, ctx->wrms_part.as<double>(), nb, ctx->n_y, span);
+                                                  wsq, 1, ctx->n_y);
+    h0_second<<<n_inst(ctx), kRedThreads, 0, ctx->stream>>>(Q, c, cp, wsq, span);
     RT_CUDA(ctx, cudaGetLastError());
     ctx->launches += 2;
     return RTBTE_OK;
@@ -530,32 +549,59 @@ CtlParams ctl_params(const rtbte_integ *o, int p) {
     return cp;
 }
 
-void ctl_reset(Ctl *c, double t0, double t_out) {
-    std::memset(c, 0, sizeof(Ctl));
-    c->t = t0;
-    c->t_out = t_out;
-    c->eps1 = c->eps2 = 1.0;
-    c->first = 1;
+void ctl_reset_all(rtbte_ctx *ctx, double t0, double t_out, long long max_steps) {
+    for (int i = 0; i < n_inst(ctx); ++i) {
+        Ctl *c = ctx->ctl_host + i;
+        const int cur = c->cur;
+        std::memset(c, 0, sizeof(Ctl));
+        c->cur = cur;
+        c->t = t0;
+        c->t_out = t_out;
+        c->eps1 = c->eps2 = 1.0;
+        c->first = 1;
+        c->max_steps = max_steps;
+    }
 }
 
-// Fixed-step RK4 of `parts` over [t0, t1] with nominal step h (last step ends at t1).
+// Fixed-step RK4 of `parts` over [t0, t1] with nominal step h (last step ends at t1), every
+// instance in lock step.  Keeps each instance's current buffer.
 int fixed_rk4(rtbte_ctx *ctx, const rtbte_integ *o, unsigned parts, double t0, double t1, double h,
               long long *attempts) {
-    Ctl *ch = ctx->ctl_host;
     int rc;
     if ((rc = read_ctl(ctx))) return rc;
-    const int cur = ch->cur;
-    ctl_reset(ch, t0, t1);
-    ch->cur = cur;
-    ch->fixed = 1;
-    ch->h = h;
-    ch->max_steps = (long long)ceil((t1 - t0) / h - 1e-9);
-    if (ch->max_steps < 1) ch->max_steps = 1;
-    ch->last = ch->max_steps == 1;
-    ch->h_try = ch->last ? t1 - t0 : h;
+    long long nsteps = (long long)ceil((t1 - t0) / h - 1e-9);
+    if (nsteps < 1) nsteps = 1;
+    ctl_reset_all(ctx, t0, t1, nsteps);
+    for (int i = 0; i < n_inst(ctx); ++i) {
+        Ctl *c = ctx->ctl_host + i;
+        c->fixed = 1;
+        c->h = h;
+        c->last = nsteps == 1;
+        c->h_try = c->last ? t1 - t0 : h;
+    }
     if ((rc = write_ctl(ctx))) return rc;
     CtlParams cp = ctl_params(o, 4);
     return run_attempts(ctx, RTBTE_RK4, cp, parts, nullptr, o->chunk > 0 ? o->chunk : 8, attempts);
+}
+
+// Aggregate per-instance controller counters into the call's statistics.
+void gather_stats(rtbte_ctx *ctx, rtbte_stats *st, bool add_steps) {
+    long long steps = 0, fails = 0;
+    double t = 1e300;
+    int status = RTBTE_OK;
+    for (int i = 0; i < n_inst(ctx); ++i) {
+        const Ctl &c = ctx->ctl_host[i];
+        steps += c.steps;
+        fails += c.fails;
+        if (c.t < t) t = c.t;
+        if (status == RTBTE_OK && c.status != RTBTE_OK) status = c.status;
+    }
+    st->steps = add_steps ? st->steps + steps : steps;
+    st->fails += fails;
+    st->t = t;
+    st->h_last = ctx->ctl_host[0].h_last;
+    st->h_next = ctx->ctl_host[0].h;
+    st->status = status;
 }
 
 }  // namespace
@@ -575,41 +621,43 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
         return fail(ctx, RTBTE_E_INVALID_ARG, "tolerances must be positive");
     const size_t nb = sizeof(double) * ctx->n_y;
     RT_CUDA(ctx, cudaMemcpyAsync(ctx->Y[0].p, y, nb, cudaMemcpyDeviceToDevice, ctx->stream));
-    Ctl *ch = ctx->ctl_host;
+    const int NI = n_inst(ctx);
+    for (int i = 0; i < NI; ++i) ctx->ctl_host[i].cur = 0;
+    const long long max_steps = o->max_steps > 0 ? o->max_steps : 1000000000LL;
+    ctl_reset_all(ctx, o->t0, t_out, max_steps);
     int rc = RTBTE_OK;
-    ctl_reset(ch, o->t0, t_out);
-    ch->max_steps = o->max_steps > 0 ? o->max_steps : 1000000000LL;
     if (m == RTBTE_RK4) {
         if ((rc = write_ctl(ctx))) return rc;
         long long att = 0;
         if ((rc = fixed_rk4(ctx, o, RTBTE_ALL, o->t0, t_out, o->h, &att))) return rc;
         st->attempts = att;
         st->rhs_full = 4 * att;
-        st->steps = ch->steps;
+        gather_stats(ctx, st, false);
     } else if (m == RTBTE_BS32 || m == RTBTE_ZON43) {
         const Tableau T = tableau_of(m);
         CtlParams cp = ctl_params(o, T.p);
         const bool est = !(o->h0 > 0);
-        if (!est) ch->h = o->hmax > 0 && o->h0 > o->hmax ? o->hmax : o->h0;
+        if (!est)
+            for (int i = 0; i < NI; ++i) ctx->ctl_host[i].h = o->hmax > 0 && o->h0 > o->hmax ? o->hmax : o->h0;
         if ((rc = write_ctl(ctx))) return rc;
         if (est) {
             if ((rc = h0_estimate(ctx, cp, RTBTE_ALL, nullptr, t_out - o->t0))) return rc;
         } else {
-            arm_kernel<<<1, 1, 0, ctx->stream>>>(ctx->ctl.as<Ctl>());
+            arm_kernel<<<(NI + 127) / 128, 128, 0, ctx->stream>>>(ctx->ctl.as<Ctl>(), NI);
             RT_CUDA(ctx, cudaGetLastError());
             ctx->launches++;
         }
         long long att = 0;
         if ((rc = run_attempts(ctx, m, cp, RTBTE_ALL, nullptr, o->chunk > 0 ? o->chunk : 8, &att))) return rc;
         st->attempts = att;
-        st->rhs_full = att * T.S + (est ? 2 : 0);
-        st->steps = ch->steps;
+        st->rhs_full = att * T.S + (est ? 2LL * NI : 0);
+        gather_stats(ctx, st, false);
     } else if (m == RTBTE_MRI_KW3) {
         const Mis M = mis_kw3();
         const int fm = o->fast_method == RTBTE_BS32 ? RTBTE_BS32 : RTBTE_ZON43;
         const Tableau Tf = tableau_of(fm);
         CtlParams cp = ctl_params(o, Tf.p);
-        ch->h = 0.0;
+        for (int i = 0; i < NI; ++i) ctx->ctl_host[i].h = 0.0;
         if ((rc = write_ctl(ctx))) return rc;
         const long long n = ctx->n_y;
         double *Fs = ctx->Fs.as<double>();
@@ -618,23 +666,23 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
         long long nsteps = (long long)ceil((t_out - o->t0) / o->h_s - 1e-9);
         if (nsteps < 1) nsteps = 1;
         double t = o->t0;
-        bool first_inner = true;
+        bool first_inner = true, failed = false;
         long long inner_attempts = 0, inner_h0 = 0;
         StageArgs a = stage_args(ctx, Tf, cp, RTBTE_SLOW, nullptr);
         a.stage = -1;
         a.respect_done = 0;
-        for (long long k = 0; k < nsteps; ++k) {
+        for (long long k = 0; k < nsteps && !failed; ++k) {
             const double H = (k == nsteps - 1) ? t_out - t : o->h_s;
             // slow RHS at z_1 = y
             if ((rc = stage(ctx, a, ctx->stream))) return rc;
             if ((rc = launch_rhs_core(ctx, RTBTE_SLOW, nullptr, ctx->stream))) return rc;
             if ((rc = launch_rows(ctx, RTBTE_SLOW, Fs, nullptr, ctx->stream))) return rc;
-            st->rhs_slow++;
+            st->rhs_slow += NI;
             for (int i = 1; i <= 3; ++i) {
                 const double dc = M.chat[i] - M.chat[i - 1];
                 const double ta = t + M.chat[i - 1] * H, tb = (i == 3) ? t + H : t + M.chat[i] * H;
                 mri_forcing<<<nb2, kRedThreads, 0, ctx->stream>>>(r, Fs, M.Om[i][0], M.Om[i][1], M.Om[i][2], i, dc, n);
-                mri_stage_reset<<<1, 1, 0, ctx->stream>>>(ctx->ctl.as<Ctl>(), cp, ta, tb);
+                mri_stage_reset<<<(NI + 127) / 128, 128, 0, ctx->stream>>>(ctx->ctl.as<Ctl>(), NI, cp, ta, tb);
                 RT_CUDA(ctx, cudaGetLastError());
                 ctx->launches += 2;
                 if (first_inner) {
@@ -645,56 +693,66 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
                 long long att = 0;
                 if ((rc = run_attempts(ctx, fm, cp, RTBTE_FAST, r, o->chunk > 0 ? o->chunk : 4, &att))) return rc;
                 inner_attempts += att;
-                if (ch->status != RTBTE_OK) break;
+                for (int q = 0; q < NI; ++q)
+                    if (ctx->ctl_host[q].status != RTBTE_OK) failed = true;
+                if (failed) break;
                 if (i < 3) {
                     if ((rc = stage(ctx, a, ctx->stream))) return rc;
                     if ((rc = launch_rhs_core(ctx, RTBTE_SLOW, nullptr, ctx->stream))) return rc;
                     if ((rc = launch_rows(ctx, RTBTE_SLOW, Fs + (long long)i * n, nullptr, ctx->stream))) return rc;
-                    st->rhs_slow++;
+                    st->rhs_slow += NI;
                 }
             }
-            if (ch->status != RTBTE_OK) break;
+            if (failed) break;
             t = (k == nsteps - 1) ? t_out : t + H;
             st->slow_steps++;
         }
         st->attempts = inner_attempts;
-        st->rhs_fast = inner_attempts * Tf.S + 2 * inner_h0;
-        st->steps = ch->steps;
-        if (ch->status == RTBTE_OK) ch->t = t;
+        st->rhs_fast = inner_attempts * Tf.S + 2LL * NI * inner_h0;
+        gather_stats(ctx, st, false);
+        if (!failed) st->t = t;
     } else {  // first-order operator splitting with RK4 (slow step, then fast sub-steps)
         if ((rc = write_ctl(ctx))) return rc;
         long long nsteps = (long long)ceil((t_out - o->t0) / o->h_s - 1e-9);
         if (nsteps < 1) nsteps = 1;
         double t = o->t0;
         long long att_s = 0, att_f = 0;
-        for (long long k = 0; k < nsteps; ++k) {
+        bool failed = false;
+        for (long long k = 0; k < nsteps && !failed; ++k) {
             const double H = (k == nsteps - 1) ? t_out - t : o->h_s;
             long long a1 = 0, a2 = 0;
             if ((rc = fixed_rk4(ctx, o, RTBTE_SLOW, t, t + H, H, &a1))) return rc;
             att_s += a1;
-            if (ch->status != RTBTE_OK) break;
+            for (int q = 0; q < NI; ++q)
+                if (ctx->ctl_host[q].status != RTBTE_OK) failed = true;
+            if (failed) break;
             long long msub = (long long)floor(H / o->h + 0.5);
             if (msub < 1) msub = 1;
             if ((rc = fixed_rk4(ctx, o, RTBTE_FAST, t, t + H, H / (double)msub, &a2))) return rc;
             att_f += a2;
-            st->steps += ch->steps;
-            if (ch->status != RTBTE_OK) break;
+            gather_stats(ctx, st, true);
+            for (int q = 0; q < NI; ++q)
+                if (ctx->ctl_host[q].status != RTBTE_OK) failed = true;
+            if (failed) break;
             t = (k == nsteps - 1) ? t_out : t + H;
             st->slow_steps++;
         }
         st->attempts = att_s + att_f;
         st->rhs_slow = 4 * att_s;
         st->rhs_fast = 4 * att_f;
-        if (ch->status == RTBTE_OK) ch->t = t;
+        const long long steps = st->steps;
+        gather_stats(ctx, st, false);
+        st->steps = steps;
+        if (!failed) st->t = t;
     }
-    st->fails = ch->fails;
-    st->t = ch->t;
-    st->h_last = ch->h_last;
-    st->h_next = ch->h;
-    // hand back the current buffer (the solution, or the last accepted state on failure)
-    RT_CUDA(ctx, cudaMemcpyAsync(y, ctx->Y[ch->cur].p, nb, cudaMemcpyDeviceToDevice, ctx->stream));
+    // hand back each instance's current buffer (the solution, or its last accepted state)
+    for (int i = 0; i < NI; ++i) {
+        const InstHost &I = ctx->inst[i];
+        const size_t off = (size_t)I.y_off, cnt = (size_t)(I.d.n_c + I.n_ph);
+        RT_CUDA(ctx, cudaMemcpyAsync(y + off, ctx->Y[ctx->ctl_host[i].cur].as<double>() + off, sizeof(double) * cnt,
+                                     cudaMemcpyDeviceToDevice, ctx->stream));
+    }
     RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    st->status = ch->status;
     if (st->status) fail(ctx, st->status, "integration stopped before t_out");
     return st->status;
 }
@@ -702,6 +760,7 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
 void destroy_graphs(rtbte_ctx *ctx) {
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
+    ctx->graph_launches.clear();
 }
 
 }  // namespace rtbte

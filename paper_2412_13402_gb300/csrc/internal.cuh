@@ -70,7 +70,7 @@ struct __align__(16) InstDev {
     long long compact_base;         // sub-lattice index of each phonon (-1: none): [n_ph]
 };
 
-// Device-side controller state of the adaptive integrators (one per context).
+// Device-side controller state of the adaptive integrators (one per instance).
 struct __align__(16) Ctl {
     double t, t_out, h, h_try;
     double eps, eps1, eps2, h_last;
@@ -182,7 +182,7 @@ struct rtbte_ctx {
     rtbte::DevBuf popf, popN, popP, instdev, compact;
     // execution plan of the RHS
     bool plan_valid = false;
-    rtbte::DevBuf items, groups, partials, eoff, poff, ppoff, cta_tab;
+    rtbte::DevBuf items, groups, partials, eoff, poff, ppoff, cta_tab, wpre, dyn_tab;
     int n_items = 0, n_groups = 0;
     int part_items[3] = {0, 0, 0};
     int part_first[3] = {0, 0, 0};
@@ -195,9 +195,10 @@ struct rtbte_ctx {
     int num_sms = 0;
     size_t smem_optin = 0;
     // integrator work buffers
-    rtbte::DevBuf Y[2], K, Fs, forcing, wrms_part, ctl, ystage, ydstage;
-    rtbte::Ctl *ctl_host = nullptr;  // pinned mirror for status reads
+    rtbte::DevBuf Y[2], K, Fs, forcing, wrms_part, ctl, ystage, ydstage;  // wrms_part: 2 x n_y squared norms
+    rtbte::Ctl *ctl_host = nullptr;  // pinned mirror of the per-instance controllers
     std::map<long long, cudaGraphExec_t> graphs;
+    std::map<long long, int> graph_launches;  // kernels per replay of each graph
     long long launches = 0;
     // collision-kernel timing (events recorded around launches outside graphs)
     bool timing = false;

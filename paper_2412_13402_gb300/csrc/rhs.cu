@@ -58,12 +58,11 @@ struct KParams {
     const Item *items;
     const Group *groups;
     int n_groups;
-    const int *warp_v;  // [grid][nwarps+1] virtual item starts of each warp for this part mask
-    int rv[3], ri[3], rlen[3];
-    int nranges;
+    const int *cta_items;  // [grid+1] first item of each CTA's range (real item indices)
+    unsigned mask;         // parts evaluated (groups of other parts are skipped)
     void *partials;
     const void *popf, *popN, *popP;
-    const Ctl *ctl;  // launches inside an integrator skip when the integration is done
+    const Ctl *ctl;  // per-instance controllers: launches inside an integrator skip finished instances
 };
 
 template <class R>
@@ -327,51 +326,92 @@ __device__ __forceinline__ void run_range(const KParams &P, const GroupView<R> &
 template <class R, bool STAGED, bool PIPE, int MINB>
 __global__ void __launch_bounds__(kRhsThreads, MINB) rhs_kernel(KParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (P.ctl && P.ctl->done) return;
     R *sm = reinterpret_cast<R *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int *wv = P.warp_v + (long long)blockIdx.x * (nwarps + 1);
-    const int c0 = wv[0], c1 = wv[nwarps];  // this CTA's virtual range
-    for (int r = 0; r < P.nranges; ++r) {
-        const int a = max(c0, P.rv[r]), b = min(c1, P.rv[r] + P.rlen[r]);
-        if (a >= b) continue;
-        const int shift = P.ri[r] - P.rv[r];
-        const int ra = a + shift, rb = b + shift;
-        int lo = 0, hi = P.n_groups - 1;  // last group with item_begin <= ra
+    const int ra = P.cta_items[blockIdx.x], rb = P.cta_items[blockIdx.x + 1];
+    if (ra >= rb) return;
+    int lo = 0, hi = P.n_groups - 1;  // last group with item_begin <= ra
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (P.groups[mid].item_begin <= ra) lo = mid; else hi = mid - 1;
+    }
+    for (int g = lo; g < P.n_groups; ++g) {
+        const Group &G = P.groups[g];
+        const int gb = G.item_begin, ge = G.item_end;
+        if (gb >= rb) break;
+        if (max(ra, gb) >= min(rb, ge)) continue;
+        if (!(P.mask & (1u << G.part))) continue;
+        if (P.ctl && P.ctl[G.inst].done) continue;  // instance already at its t_out
+        GroupView<R> V;
+        V.idx = G.idx;
+        V.W = reinterpret_cast<const R *>(G.W);
+        V.part = G.part;
+        V.sb = G.s_bits;
+        V.pb = G.pp_bits;
+        V.Nglob = reinterpret_cast<const R *>(P.popN) + G.N_inst;
+        const R *src0 = reinterpret_cast<const R *>(G.part == PART_PP ? P.popP : P.popf) + G.stage0_src;
+        const R *src1 = reinterpret_cast<const R *>(P.popN) + G.stage1_src;
+        if (STAGED) {
+            const int l0 = G.stage0_len, l1 = G.stage1_len;
+            __syncthreads();  // the previous group's readers are done with the buffer
+            stage_copy<R>(sm, src0, l0);
+            if (l1 > 0) stage_copy<R>(sm + l0, src1, l1);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            __syncthreads();
+            V.s0 = sm;
+            V.s1 = sm + l0;
+        } else {
+            V.s0 = src0;
+            V.s1 = src1;
+        }
+        run_range<R, PIPE>(P, V, max(ra, gb) + warp, min(rb, ge), nwarps, lane);
+    }
+}
+
+// Work split over the groups still active (instance not done, part in the mask), recomputed
+// on the device before a collision launch inside a batched integration: CTA c gets the items
+// whose cumulative active weight falls in [c, c+1) * total / grid.  One block.
+__global__ void split_kernel(const Group *groups, int n_groups, const long long *wpre, const Ctl *ctl, unsigned mask,
+                             int grid, int n_items, int *out) {
+    __shared__ long long A[1025];
+    const int T = blockDim.x;
+    // active weight of each group; n_groups <= 1024 (checked on the host)
+    for (int g = threadIdx.x; g < n_groups; g += T) {
+        const Group &G = groups[g];
+        const bool on = (mask & (1u << G.part)) && !ctl[G.inst].done;
+        A[g + 1] = on ? wpre[G.item_end] - wpre[G.item_begin] : 0;
+    }
+    if (threadIdx.x == 0) {
+        A[0] = 0;
+        for (int g = 0; g < n_groups; ++g) A[g + 1] += A[g];  // a few hundred groups: serial scan
+    }
+    __syncthreads();
+    const long long total = A[n_groups];
+    for (int c = threadIdx.x; c <= grid; c += T) {
+        if (total == 0) {
+            out[c] = 0;
+            continue;
+        }
+        if (c == grid) {
+            out[c] = n_items;
+            continue;
+        }
+        const long long t = total * c / grid;
+        int lo = 0, hi = n_groups - 1;  // group g with A[g] <= t < A[g+1]
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
-            if (P.groups[mid].item_begin <= ra) lo = mid; else hi = mid - 1;
+            if (A[mid] <= t) lo = mid; else hi = mid - 1;
         }
-        for (int g = lo; g < P.n_groups; ++g) {
-            const Group &G = P.groups[g];
-            const int gb = G.item_begin, ge = G.item_end;
-            if (gb >= rb) break;
-            if (max(ra, gb) >= min(rb, ge)) continue;
-            GroupView<R> V;
-            V.idx = G.idx;
-            V.W = reinterpret_cast<const R *>(G.W);
-            V.part = G.part;
-            V.sb = G.s_bits;
-            V.pb = G.pp_bits;
-            V.Nglob = reinterpret_cast<const R *>(P.popN) + G.N_inst;
-            const R *src0 = reinterpret_cast<const R *>(G.part == PART_PP ? P.popP : P.popf) + G.stage0_src;
-            const R *src1 = reinterpret_cast<const R *>(P.popN) + G.stage1_src;
-            if (STAGED) {
-                const int l0 = G.stage0_len, l1 = G.stage1_len;
-                __syncthreads();  // the previous group's readers are done with the buffer
-                stage_copy<R>(sm, src0, l0);
-                if (l1 > 0) stage_copy<R>(sm + l0, src1, l1);
-                asm volatile("cp.async.commit_group;\n" ::: "memory");
-                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-                __syncthreads();
-                V.s0 = sm;
-                V.s1 = sm + l0;
-            } else {
-                V.s0 = src0;
-                V.s1 = src1;
-            }
-            run_range<R, PIPE>(P, V, max(ra, gb) + warp, min(rb, ge), nwarps, lane);
+        while (lo < n_groups - 1 && A[lo + 1] == A[lo]) ++lo;  // skip inactive groups
+        const Group &G = groups[lo];
+        const long long w = wpre[G.item_begin] + (t - A[lo]);
+        int a = G.item_begin, b = G.item_end;  // first item with wpre >= w
+        while (a < b) {
+            int mid = (a + b) >> 1;
+            if (wpre[mid] < w) a = mid + 1; else b = mid;
         }
+        out[c] = c == 0 ? 0 : a;
     }
 }
 
@@ -428,36 +468,49 @@ RowParams row_params(rtbte_ctx *ctx) {
 // by the same weights).
 int split_tables(rtbte_ctx *ctx, int overhead) {
     const int G = ctx->grid;
-    const int NW = kRhsThreads / 32;
     const std::vector<unsigned short> &len = ctx->item_len_h;
-    std::vector<int> tab(7LL * G * (NW + 1), 0);
-    std::vector<long long> vpre;
+    const int n = (int)len.size();
+    // item weight prefix (all parts), used by the host split below and the device split
+    std::vector<long long> wpre(n + 1, 0);
+    for (int part = 0; part < 3; ++part) {
+        const long long sc = (long long)(64.0 * ctx->part_scale[part] + 0.5);  // cost per entry-equivalent
+        for (int k = ctx->part_first[part]; k < ctx->part_first[part] + ctx->part_items[part]; ++k)
+            wpre[k + 1] = sc * (len[k] + overhead);
+    }
+    for (int k = 0; k < n; ++k) wpre[k + 1] += wpre[k];
+    std::vector<int> tab(7LL * (G + 1), 0);
+    std::vector<long long> apre;  // prefix of the enabled parts' weights, item order
+    std::vector<int> aidx;
     for (unsigned mask = 1; mask <= 7; ++mask) {
-        vpre.assign(1, 0);
+        apre.assign(1, 0);
+        aidx.clear();
         for (int part = 0; part < 3; ++part) {
             if (!(mask & (1u << part))) continue;
-            const long long sc = (long long)(64.0 * ctx->part_scale[part] + 0.5);  // cost per entry-equivalent
-            for (int k = ctx->part_first[part]; k < ctx->part_first[part] + ctx->part_items[part]; ++k)
-                vpre.push_back(vpre.back() + sc * (len[k] + overhead));
+            for (int k = ctx->part_first[part]; k < ctx->part_first[part] + ctx->part_items[part]; ++k) {
+                apre.push_back(apre.back() + (wpre[k + 1] - wpre[k]));
+                aidx.push_back(k);
+            }
         }
-        const long long total = vpre.back();
-        const int nv = (int)vpre.size() - 1;
-        auto at = [&](long long target) {
-            int k = (int)(std::lower_bound(vpre.begin(), vpre.end(), target) - vpre.begin());
-            return std::min(k, nv);
-        };
-        int *t = tab.data() + (long long)(mask - 1) * G * (NW + 1);
-        for (int c = 0; c < G; ++c) {
-            const long long c0 = total * c / G, c1 = total * (c + 1) / G;
-            const int v0 = c == 0 ? 0 : at(c0), v1 = c == G - 1 ? nv : at(c1);
-            const long long w0 = vpre[v0], w1 = vpre[v1];
-            int *row = t + (long long)c * (NW + 1);
-            row[0] = v0;
-            row[NW] = v1;
-            for (int w = 1; w < NW; ++w) row[w] = std::max(v0, std::min(v1, at(w0 + (w1 - w0) * w / NW)));
+        const long long total = apre.back();
+        const int na = (int)aidx.size();
+        int *t = tab.data() + (long long)(mask - 1) * (G + 1);
+        for (int c = 0; c <= G; ++c) {
+            if (na == 0) {
+                t[c] = 0;
+                continue;
+            }
+            if (c == G) {
+                t[c] = n;
+                continue;
+            }
+            const long long target = total * c / G;
+            const int j = (int)(std::lower_bound(apre.begin(), apre.end(), target) - apre.begin());
+            t[c] = c == 0 ? 0 : (j >= na ? n : aidx[j]);
         }
     }
     ctx->item_overhead = overhead;
+    int rc;
+    if ((rc = upload_vec(ctx, ctx->wpre, wpre))) return rc;
     return upload_vec(ctx, ctx->cta_tab, tab);
 }
 
@@ -610,6 +663,10 @@ int make_plan(rtbte_ctx *ctx) {
     if ((rc = upload_vec(ctx, ctx->instdev, idev))) return rc;
     if ((rc = upload_vec(ctx, ctx->compact, compact))) return rc;
     if ((rc = split_tables(ctx, ctx->item_overhead))) return rc;
+    if (ctx->n_groups > 1024) return fail(ctx, RTBTE_E_UNSUPPORTED, "more than 1024 staging groups");
+    ctx->dyn_tab.release();
+    RT_CUDA(ctx, cudaMalloc(&ctx->dyn_tab.p, sizeof(int) * (ctx->grid + 1)));
+    ctx->dyn_tab.bytes = sizeof(int) * (ctx->grid + 1);
     ctx->partials.release();
     size_t pb = std::max<size_t>(2 * R * (size_t)std::max(ctx->n_items, 1), 16);
     RT_CUDA(ctx, cudaMalloc(&ctx->partials.p, pb));
@@ -648,16 +705,16 @@ static int launch_core_t(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStr
     P.items = ctx->items.as<Item>();
     P.groups = ctx->groups.as<Group>();
     P.n_groups = ctx->n_groups;
-    P.warp_v = ctx->cta_tab.as<int>() + (long long)(parts - 1) * ctx->grid * (kRhsThreads / 32 + 1);
-    int v = 0;
-    for (int part = 0; part < 3; ++part)
-        if (parts & (1u << part)) {
-            P.rv[P.nranges] = v;
-            P.ri[P.nranges] = ctx->part_first[part];
-            P.rlen[P.nranges] = ctx->part_items[part];
-            v += ctx->part_items[part];
-            P.nranges++;
-        }
+    P.mask = parts;
+    if (ctl && ctx->inst.size() > 1) {  // batched integration: balance over the active instances
+        split_kernel<<<1, 256, 0, s>>>(ctx->groups.as<Group>(), ctx->n_groups, ctx->wpre.as<long long>(), ctl, parts,
+                                       ctx->grid, ctx->n_items, ctx->dyn_tab.as<int>());
+        RT_CUDA(ctx, cudaGetLastError());
+        ctx->launches++;
+        P.cta_items = ctx->dyn_tab.as<int>();
+    } else {
+        P.cta_items = ctx->cta_tab.as<int>() + (long long)(parts - 1) * (ctx->grid + 1);
+    }
     P.partials = ctx->partials.p;
     P.popf = ctx->popf.p;
     P.popN = ctx->popN.p;

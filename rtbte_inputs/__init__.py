@@ -364,6 +364,25 @@ def tiny(n=(4, 4, 1), nbands: int = 2, nmodes: int = 3, fold: int = 1, pp_stride
     )
 
 
+def ensemble(n_inst: int = 64, seed: int = SEED_BASE + 3, sides=tuple(range(24, 97, 3))) -> list:
+    """Batched ensemble: independent graphene-like instances with uneven grids (side drawn
+    uniformly from `sides`), excitation energies E_x ~ U[0.1, 1.0] eV and temperatures
+    T ~ U[100, 500] K drawn from the seed.  Broadenings scale as sqrt(180/side) so that coarse
+    grids keep resonant channels (sigma_eph = 20 meV and sigma_pp = 2 meV at side 180)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_inst):
+        n = int(rng.choice(sides))
+        E_x = float(rng.uniform(0.1, 1.0))
+        T = float(rng.uniform(100.0, 500.0))
+        f = math.sqrt(180.0 / n)
+        m = graphene(n=n, window=1.0, seed=seed * 1000 + i, T=T, E_x=E_x, sigma_eph=0.020 * f, sigma_pp=0.002 * f)
+        m.name = f"ensemble{i}_n{n}"
+        m.note = f"config 4 instance {i}: side {n}, E_x {E_x:.3f} eV, T {T:.1f} K"
+        out.append(m)
+    return out
+
+
 def random_populations(model: Model, seed: int, spread: float = 1.0):
     """Seeded random populations of the model's shape: f in (0.02, 0.98), N in (0, 3*spread),
     zero on frozen phonon states."""

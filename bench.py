@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--accuracy-only", action="store_true", help="print only the error-versus-cost sweep")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: only standalone full-RHS evaluations (warm-up + steps), no JSON line")
     ap.add_argument("--grid", type=int, default=180, help="k/q grid side of the graphene-like workload (profiling)")
@@ -280,6 +282,71 @@ def run_ensemble(args, rt, ri, dev, peak):
             "rhs_kernel": {"avg_launch_ms": kms / kn, "achieved_gbs": ach, "frac_of_measured_peak": ach / peak}}
 
 
+def accuracy_sweep(rt, ri, dev, t_end=0.5):
+    """Error-versus-cost protocol of the paper (errors at t_end = 0.5 ps, relative L2 of the
+    carrier and of the phonon populations against a reference).  Reference: FP64 collision
+    sums, adaptive Zonneveld with rtol 1e-9, atol 1e-15.  For each method and precision the
+    cheapest setting with both errors <= 1e-6 gives the simulated ps per wall-second."""
+    import numpy as np
+    import torch
+
+    m = ri.graphene()
+    y0 = torch.tensor(m.y0(), device=dev)
+    nc = m.n_c
+
+    def run(ctx, **kw):
+        y = y0.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        st = ctx.advance_to(t_end, y, t0=0.0, **kw)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        return y.cpu().numpy(), st, e0.elapsed_time(e1) / 1000.0
+
+    ctxs = {}
+    for prec in ("fp64", "fp32"):
+        c = rt.Context(m, precision=prec, device=dev.index or 0)
+        c.upload_channels()
+        c.rhs(y0, torch.empty_like(y0))
+        c.autotune(rt.RTBTE_ALL)
+        ctxs[prec] = c
+    ref, st_ref, t_ref = run(ctxs["fp64"], method="zon43", rtol=1e-9, atol_c=1e-15, atol_ph=1e-15)
+    assert st_ref["status"] == 0, st_ref
+
+    def err(y):
+        ec = np.linalg.norm(y[:nc] - ref[:nc]) / np.linalg.norm(ref[:nc])
+        ep = np.linalg.norm(y[nc:] - ref[nc:]) / np.linalg.norm(ref[nc:])
+        return float(ec), float(ep)
+
+    settings = [("fp32", "erk", dict(method="zon43", rtol=r, atol_c=1e-15, atol_ph=1e-15)) for r in
+                (1e-4, 1e-5, 1e-6, 1e-7)]
+    settings += [("fp32", "mri", dict(method="mri", h_s=hs * 1e-3, rtol=r, atol_c=1e-9, atol_ph=1e-12))
+                 for hs in (50.0, 20.0, 10.0) for r in (1e-5, 1e-6)]
+    settings += [("fp32", "rk4", dict(method="rk4", h=h * 1e-3)) for h in (5.0, 2.0, 1.0)]
+    settings += [("fp64", "erk", dict(method="zon43", rtol=r, atol_c=1e-15, atol_ph=1e-15)) for r in (1e-5, 1e-6)]
+    settings += [("fp64", "mri", dict(method="mri", h_s=20e-3, rtol=1e-6, atol_c=1e-9, atol_ph=1e-12))]
+    runs = []
+    for prec, fam, kw in settings:
+        y, st, sec = run(ctxs[prec], **kw)
+        ec, ep = err(y) if st["status"] == 0 else (float("inf"), float("inf"))
+        runs.append({"precision": prec, "method": fam, **{k: v for k, v in kw.items() if k != "method"},
+                     "status": st["status"], "err_carriers": ec, "err_phonons": ep, "seconds": sec,
+                     "steps": st["steps"], "rhs_full": st["rhs_full"], "rhs_fast": st["rhs_fast"],
+                     "rhs_slow": st["rhs_slow"]})
+    for c in ctxs.values():
+        c.close()
+    best = {}
+    for r in runs:
+        if r["status"] == 0 and max(r["err_carriers"], r["err_phonons"]) <= 1e-6:
+            key = f'{r["method"]}_{r["precision"]}'
+            if key not in best or r["seconds"] < best[key]["seconds"]:
+                best[key] = r
+    return {"t_end_ps": t_end, "reference": {"method": "zon43", "precision": "fp64", "rtol": 1e-9,
+                                             "atol": 1e-15, "seconds": t_ref, "steps": st_ref["steps"]},
+            "runs": runs, "sim_ps_per_s_at_1e-6": {k: t_end / v["seconds"] for k, v in best.items()}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -406,6 +473,9 @@ def run_ours(args):
     mri = {"sim_ps_per_s": mri_steps * hs / (mri_ms / 1000.0), "h_s_fs": hs * 1000, "slow_steps": st["slow_steps"],
            "rhs_fast": st["rhs_fast"], "rhs_slow": st["rhs_slow"], "fast_steps": st["steps"], "ms": mri_ms}
 
+    # ---- error-versus-cost: simulated ps per second at population error <= 1e-6
+    acc = accuracy_sweep(rt, ri, dev) if (rank == 0 and not args.no_accuracy) else None
+
     # ---- batched ensemble: 64 independent instances of uneven size, one persistent launch
     # per RHS, per-instance adaptive controllers
     ens = run_ensemble(args, rt, ri, dev, peak) if not args.no_ensemble else None
@@ -428,7 +498,9 @@ def run_ours(args):
                            "channel_entries": entries, "replicas": world, "parallelism": f"replicas x{world}",
                            "autotuned_split_weight": split_weight},
                 "sim_ps_per_s": sim_ps * world / (tmax / 1000.0), "rhs_evals_timed": tot_rhs,
-                "roofline": roofline, "e2e": e2e, "mri": mri, "ensemble": ens, "clocks": clk.summary(),
+                "sim_ps_per_s_at_rel_err_1e-6": (max(acc["sim_ps_per_s_at_1e-6"].values())
+                                                 if acc and acc["sim_ps_per_s_at_1e-6"] else None),
+                "roofline": roofline, "e2e": e2e, "mri": mri, "accuracy": acc, "ensemble": ens, "clocks": clk.summary(),
                 "gpu_launches": launches,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
@@ -442,6 +514,14 @@ def main():
     args = parse()
     if args.profile:
         return run_profile(args)
+    if args.accuracy_only:
+        import torch
+
+        import paper_2412_13402_gb300 as rt
+        import rtbte_inputs as ri
+
+        print(json.dumps(accuracy_sweep(rt, ri, torch.device("cuda", 0))), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

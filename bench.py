@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--accuracy-only", action="store_true", help="print only the error-versus-cost sweep")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: only standalone full-RHS evaluations (warm-up + steps), no JSON line")
@@ -282,6 +283,9 @@ def run_ensemble(args, rt, ri, dev, peak):
             "rhs_kernel": {"avg_launch_ms": kms / kn, "achieved_gbs": ach, "frac_of_measured_peak": ach / peak}}
 
 
+_REFERENCE = {}  # t_end -> FP64 tight-tolerance reference state of the graphene workload
+
+
 def accuracy_sweep(rt, ri, dev, t_end=0.5):
     """Error-versus-cost protocol of the paper (errors at t_end = 0.5 ps, relative L2 of the
     carrier and of the phonon populations against a reference).  Reference: FP64 collision
@@ -313,6 +317,7 @@ def accuracy_sweep(rt, ri, dev, t_end=0.5):
         ctxs[prec] = c
     ref, st_ref, t_ref = run(ctxs["fp64"], method="zon43", rtol=1e-9, atol_c=1e-15, atol_ph=1e-15)
     assert st_ref["status"] == 0, st_ref
+    _REFERENCE[t_end] = ref
 
     def err(y):
         ec = np.linalg.norm(y[:nc] - ref[:nc]) / np.linalg.norm(ref[:nc])
@@ -345,6 +350,101 @@ def accuracy_sweep(rt, ri, dev, t_end=0.5):
     return {"t_end_ps": t_end, "reference": {"method": "zon43", "precision": "fp64", "rtol": 1e-9,
                                              "atol": 1e-15, "seconds": t_ref, "steps": st_ref["steps"]},
             "runs": runs, "sim_ps_per_s_at_1e-6": {k: t_end / v["seconds"] for k, v in best.items()}}
+
+
+def surrogate_study(rt, ri, dev, t_end=0.5, h_s=0.020, period=10):
+    """The learned slow stage on the same workload and error protocol.  Pairs (N, exact
+    I^{ph-ph}) come from the method's own trajectories (6 initial conditions, 21 states
+    each, 10 fs apart); the network (4 periodic 3x3 conv layers of width 64, pointwise MLP)
+    is trained by librtbte's BF16 tensor-core kernels, first on single pairs, then on
+    differences along a trajectory.  A/B over t_end: plain MRI (exact slow part at every
+    stage), MRI with the surrogate's control variate (exact judge every `period` slow steps),
+    and the same schedule with the network's output zeroed (the exact value held between
+    judges), errors against the FP64 reference."""
+    import numpy as np
+    import torch
+
+    m = ri.graphene()
+    nc = m.n_c
+    ctx = rt.Context(m, precision="fp32", device=dev.index or 0)
+    ctx.upload_channels()
+    ctx.autotune(rt.RTBTE_ALL)
+    y0 = torch.tensor(m.y0(), device=dev)
+    if t_end not in _REFERENCE:
+        ref_ctx = rt.Context(m, precision="fp64", device=dev.index or 0)
+        ref_ctx.upload_channels()
+        yr = y0.clone()
+        assert ref_ctx.advance_to(t_end, yr, t0=0.0, method="zon43", rtol=1e-9, atol_c=1e-15,
+                                  atol_ph=1e-15)["status"] == 0
+        ref_ctx.close()
+        _REFERENCE[t_end] = yr.cpu().numpy()
+    ref = _REFERENCE[t_end]
+
+    def timed(fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        for _ in range(n):
+            fn()
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    t0 = time.time()
+    states = []
+    for j in range(6):
+        mj = ri.graphene(E_x=0.5 + 0.1 * j, amp=0.15 + 0.05 * j, T=220.0 + 30 * j)
+        yj = torch.tensor(mj.y0(), device=dev)
+        states.append((yj.clone(), j))
+        for i in range(1, 21):
+            assert ctx.advance_to(0.01 * i, yj, t0=0.01 * (i - 1), method="zon43", **TOL)["status"] == 0
+            states.append((yj.clone(), j))
+    sur = rt.Surrogate(ctx, width=64, capacity=len(states), seed=3)
+    for yy, j in states:
+        sur.collect(yy, j)
+    torch.cuda.synchronize()
+    collect_s = time.time() - t0
+    t0 = time.time()
+    l_abs = sur.train(2000, 4, 1e-3)
+    l_diff = sur.train(2000, 4, 5e-4, horizon=4)
+    train_s = time.time() - t0
+    yd = torch.empty_like(y0)
+    exact_ms = timed(lambda: ctx.rhs(y0, yd, parts=rt.RTBTE_SLOW), 50)
+    infer_ms = timed(lambda: sur.predict(y0), 50)
+
+    def run(tag, attach):
+        if attach:
+            sur.attach(judge_period=period, judge_tol=10.0)
+        y = y0.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        st = ctx.advance_to(t_end, y, t0=0.0, method="mri", h_s=h_s, **TOL)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        sur.detach()
+        sec = e0.elapsed_time(e1) / 1000.0
+        yy = y.cpu().numpy()
+        return {"variant": tag, "status": st["status"], "seconds": sec, "sim_ps_per_s": t_end / sec,
+                "err_carriers": float(np.linalg.norm(yy[:nc] - ref[:nc]) / np.linalg.norm(ref[:nc])),
+                "err_phonons": float(np.linalg.norm(yy[nc:] - ref[nc:]) / np.linalg.norm(ref[nc:])),
+                "slow_exact": st["slow_exact"], "slow_surrogate": st["slow_surrogate"],
+                "judge_err_max": st["judge_err_max"], "rhs_fast": st["rhs_fast"]}
+
+    ab = [run("plain MRI", False), run("surrogate MRI", True)]
+    p = sur.get_params()
+    held = p.copy()
+    held[-(64 * m.nmodes + m.nmodes):] = 0.0
+    sur.set_params(held)
+    ab.append(run("held exact value (network output zeroed)", True))
+    sur.set_params(p)
+    sur.close()
+    ctx.close()
+    return {"pairs": len(states), "collect_s": collect_s, "train_steps": [2000, 2000], "batch": 4, "train_s": train_s,
+            "loss_abs": l_abs, "loss_diff": l_diff, "exact_slow_ms": exact_ms, "inference_ms": infer_ms,
+            "t_end_ps": t_end, "h_s_fs": h_s * 1000, "judge_period": period, "ab": ab}
 
 
 def run_ours(args):
@@ -480,6 +580,9 @@ def run_ours(args):
     # per RHS, per-instance adaptive controllers
     ens = run_ensemble(args, rt, ri, dev, peak) if not args.no_ensemble else None
 
+    # ---- learned slow stage (neural-operator surrogate of ph-ph inside MRI)
+    surr = surrogate_study(rt, ri, dev) if (rank == 0 and not args.no_surrogate) else None
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -500,7 +603,8 @@ def run_ours(args):
                 "sim_ps_per_s": sim_ps * world / (tmax / 1000.0), "rhs_evals_timed": tot_rhs,
                 "sim_ps_per_s_at_rel_err_1e-6": (max(acc["sim_ps_per_s_at_1e-6"].values())
                                                  if acc and acc["sim_ps_per_s_at_1e-6"] else None),
-                "roofline": roofline, "e2e": e2e, "mri": mri, "accuracy": acc, "ensemble": ens, "clocks": clk.summary(),
+                "roofline": roofline, "e2e": e2e, "mri": mri, "accuracy": acc, "ensemble": ens, "surrogate": surr,
+                "clocks": clk.summary(),
                 "gpu_launches": launches,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -175,7 +175,9 @@ typedef struct rtbte_stats {
     double t;                            /* time of the returned y                        */
     double h_last, h_next;               /* last accepted step, next proposal             */
     int32_t status;                      /* same as the return value                      */
-    int32_t reserved;
+    int32_t surrogate_fallbacks;         /* MRI calls that detached the surrogate (0/1)   */
+    int64_t slow_exact, slow_surrogate;  /* MRI slow stages: exact / surrogate values     */
+    double judge_err_max;                /* largest relative error seen by a judge (or -1)*/
 } rtbte_stats;
 
 typedef struct rtbte_ctx rtbte_ctx;
@@ -274,6 +276,74 @@ const char *rtbte_status_string(int status);
 #define RTBTE_NOALLOC_SCRATCH_BYTES (8u << 20)
 int rtbte_eph_rhs_noalloc(int32_t n_c, int64_t n_ph, int32_t nmodes, const int64_t *off, const int32_t *src,
                           const int32_t *ph, const double *W, const double *y, double *ydot, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Neural-operator surrogate of the ph-ph integral (the learned part of this library; the
+ * paper has none).  A periodic-convolution network maps the phonon populations of one
+ * instance's ph-ph sub-lattice (one channel per branch, nq_s[0] x nq_s[1], 2-D models only)
+ * to I^{ph-ph} (Eq. ph-ph) on that sub-lattice:
+ *   x = (N - mu)/sd;  h_l = tanh(conv3x3_periodic(h_{l-1}) + b_l), l = 1..4 (C -> w -> w -> w -> w);
+ *   h5 = tanh(h4 M1 + c1);  out = h5 M2 + c2;  I = out * so      (C = nmodes, w = width)
+ * Training and inference run on the GPU: every product is a BF16 tensor-core GEMM with FP32
+ * accumulation; master weights, Adam moments and activations are FP32.  Parameters in the
+ * logical order W1 [9, C, w], b1 [w], W2 [9, w, w], b2, W3, b3, W4, b4, M1 [w, w], c1 [w],
+ * M2 [w, C], c2 [C] (row-major; tap = (dy+1)*3 + (dx+1), tap input (y+dy, x+dx) mod n).
+ * Sample arrays are [B, nq_s[1], nq_s[0], C] (x fastest, channel innermost). */
+typedef struct rtbte_surrogate rtbte_surrogate;
+
+/* Create a surrogate for instance `inst` of `ctx` (which must outlive it): width w (multiple
+ * of 8, 8..256), room for `capacity` collected pairs, weights N(0, 1/fan_in) from `seed`
+ * (last layer x0.1), biases 0.  Errors: INVALID_ARG, UNSUPPORTED (no sub-lattice, dim != 2,
+ * more than 16 branches), OOM/CUDA. */
+int rtbte_surrogate_create(rtbte_ctx *ctx, int inst, int width, int capacity, uint64_t seed, rtbte_surrogate **out);
+
+/* Evaluate the exact slow part (RTBTE_SLOW) at the DEVICE state y (FP64 [n_y]) and store the
+ * pair (N, I^{ph-ph}) of the surrogate's instance, in FP32, on the device, tagged with the
+ * caller's trajectory id (pairs are numbered in collection order).  Enqueued on the context's
+ * stream.  Errors: INVALID_ARG (NULL or buffer full), those of rtbte_rhs. */
+int rtbte_surrogate_collect(rtbte_surrogate *s, const double *y, int trajectory);
+
+/* `steps` Adam steps (beta 0.9/0.999, eps 1e-8, learning rate lr), each on `batch` training
+ * units drawn without replacement per epoch (seeded shuffle).  horizon = 0: a unit is one
+ * collected pair and the loss is mean((out - I/so)^2).  horizon > 0: a unit is two pairs i < j
+ * of one trajectory with j - i <= horizon and the loss is the mean square of
+ * (out_j - out_i) - (I_j - I_i)/so, the quantity the control variate uses.  The first call fixes
+ * the per-channel normalisation (mu, sd of N; so = RMS of I) from the pairs collected so far.
+ * Synchronises; *loss_out (may be NULL) = the loss of the last minibatch.
+ * Errors: INVALID_ARG, STATE (no pairs / no units), OOM/CUDA. */
+int rtbte_surrogate_train(rtbte_surrogate *s, int steps, int batch, int horizon, float lr, float *loss_out);
+
+/* out (DEVICE FP64 [n_y]) = the surrogate's I^{ph-ph} on the instance's sub-lattice rows and 0
+ * on every other row, for the DEVICE state y.  Enqueued on the context's stream. */
+int rtbte_surrogate_predict(rtbte_surrogate *s, const double *y, double *out);
+
+/* Loss and gradients for HOST inputs: x, t FP32 [B, nq_s[1], nq_s[0], C], already normalised
+ * (x rounded to BF16 on the device).  *loss = mean((out - t)^2); grad (may be NULL) receives
+ * rtbte_surrogate_num_params() FP32 values in the logical order; out (may be NULL) receives
+ * the network output FP32 [B, ..., C].  Synchronises. */
+int rtbte_surrogate_loss_grad(rtbte_surrogate *s, const float *x, const float *t, int B, float *loss, float *grad,
+                              float *out);
+int64_t rtbte_surrogate_num_params(const rtbte_surrogate *s);
+/* Copy the FP32 master weights to / from host memory (logical order); set refreshes the BF16 copy. */
+int rtbte_surrogate_get_params(rtbte_surrogate *s, float *host);
+int rtbte_surrogate_set_params(rtbte_surrogate *s, const float *host);
+/* Normalisation (arrays of nmodes, may be NULL) and the number of collected pairs. */
+void rtbte_surrogate_stats(const rtbte_surrogate *s, float *mu, float *sd, float *so, int *count);
+
+/* Use `s` (NULL detaches) for the slow part of RTBTE_METHOD_MRI_KW3 integrations of this
+ * context (single-instance contexts; the surrogate's instance must be 0).  Each slow step
+ * takes f^s(Y) = I_exact(Y_ref) + S(Y) - S(Y_ref) (control variate about the reference
+ * state Y_ref of the last exact evaluation, S = the surrogate).  Every `judge_period` slow
+ * steps the exact integral is evaluated at the step's start state: it becomes the new
+ * reference, and if the relative 2-norm error of the control-variate value against it
+ * exceeds `judge_tol`, the surrogate is detached for the rest of the call (exact slow part;
+ * reported in rtbte_stats.surrogate_fallbacks).  Width 64 runs the fused single-sample
+ * inference kernels (four launches per value); other widths the training kernels.
+ * Errors: INVALID_ARG, STATE (untrained), UNSUPPORTED. */
+int rtbte_set_surrogate(rtbte_ctx *ctx, rtbte_surrogate *s, int judge_period, double judge_tol);
+
+/* Release the surrogate's device memory (NULL is ignored). */
+void rtbte_surrogate_destroy(rtbte_surrogate *s);
 
 /* Release every device and host resource of the context (NULL is ignored). */
 void rtbte_destroy(rtbte_ctx *ctx);

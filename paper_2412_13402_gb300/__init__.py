@@ -35,7 +35,10 @@ HBAR_EV_PS = 6.582119569e-4
 EXPORTS = ["rtbte_desc_defaults", "rtbte_integ_defaults", "rtbte_create", "rtbte_upload_channels", "rtbte_rhs",
            "rtbte_advance_to", "rtbte_get_sizes", "rtbte_download_channels", "rtbte_set_stream",
            "rtbte_autotune", "rtbte_set_kernel_timing", "rtbte_kernel_time", "rtbte_launch_count", "rtbte_last_error",
-           "rtbte_status_string", "rtbte_eph_rhs_noalloc", "rtbte_destroy"]
+           "rtbte_status_string", "rtbte_eph_rhs_noalloc", "rtbte_surrogate_create", "rtbte_surrogate_collect",
+           "rtbte_surrogate_train", "rtbte_surrogate_predict", "rtbte_surrogate_loss_grad",
+           "rtbte_surrogate_num_params", "rtbte_surrogate_get_params", "rtbte_surrogate_set_params",
+           "rtbte_surrogate_stats", "rtbte_set_surrogate", "rtbte_surrogate_destroy", "rtbte_destroy"]
 
 
 class InstanceDesc(C.Structure):
@@ -78,10 +81,12 @@ class Integ(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("attempts", C.c_int64), ("fails", C.c_int64), ("rhs_full", C.c_int64),
                 ("rhs_fast", C.c_int64), ("rhs_slow", C.c_int64), ("slow_steps", C.c_int64), ("t", C.c_double),
-                ("h_last", C.c_double), ("h_next", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32)]
+                ("h_last", C.c_double), ("h_next", C.c_double), ("status", C.c_int32),
+                ("surrogate_fallbacks", C.c_int32), ("slow_exact", C.c_int64), ("slow_surrogate", C.c_int64),
+                ("judge_err_max", C.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lock = threading.Lock()
@@ -123,6 +128,21 @@ def load():
         L.rtbte_status_string.argtypes = [i32]
         L.rtbte_status_string.restype = C.c_char_p
         L.rtbte_eph_rhs_noalloc.argtypes = [C.c_int32, i64, C.c_int32, vp, vp, vp, vp, vp, vp, vp]
+        fp = C.c_float
+        L.rtbte_surrogate_create.argtypes = [vp, i32, i32, i32, C.c_uint64, C.POINTER(vp)]
+        L.rtbte_surrogate_collect.argtypes = [vp, vp, i32]
+        L.rtbte_surrogate_train.argtypes = [vp, i32, i32, i32, fp, vp]
+        L.rtbte_surrogate_predict.argtypes = [vp, vp, vp]
+        L.rtbte_surrogate_loss_grad.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+        L.rtbte_surrogate_num_params.argtypes = [vp]
+        L.rtbte_surrogate_num_params.restype = i64
+        L.rtbte_surrogate_get_params.argtypes = [vp, vp]
+        L.rtbte_surrogate_set_params.argtypes = [vp, vp]
+        L.rtbte_surrogate_stats.argtypes = [vp, vp, vp, vp, vp]
+        L.rtbte_surrogate_stats.restype = None
+        L.rtbte_set_surrogate.argtypes = [vp, vp, i32, dbl]
+        L.rtbte_surrogate_destroy.argtypes = [vp]
+        L.rtbte_surrogate_destroy.restype = None
         L.rtbte_destroy.argtypes = [vp]
         L.rtbte_destroy.restype = None
         _lib = L
@@ -349,3 +369,84 @@ def _mode_blocked_eph(model, e):
     np.cumsum(cnt, out=off[1:])
     return (off, np.ascontiguousarray(src[order], np.int32), np.ascontiguousarray(ph[order], np.int32),
             np.ascontiguousarray(W[order], np.float64))
+
+
+class Surrogate:
+    """Neural-operator surrogate of the ph-ph integral of instance `inst` of a Context
+    (2-D sub-lattice, one channel per branch).  Training and inference run in librtbte's
+    BF16 tensor-core kernels; this class only marshals arguments."""
+
+    def __init__(self, ctx: "Context", inst: int = 0, width: int = 64, capacity: int = 1024, seed: int = 0):
+        self.context = ctx
+        m = ctx.models[inst]
+        self.nmodes = m.nmodes
+        self.nq_s = tuple(n // m.pp_stride if n > 1 else 1 for n in m.nq)
+        h = C.c_void_p()
+        _check(ctx.ctx, load().rtbte_surrogate_create(ctx.ctx, inst, width, capacity, seed, C.byref(h)))
+        self.h = h
+
+    def _chk(self, rc):
+        if rc != RTBTE_OK:
+            raise RtbteError(rc, load().rtbte_last_error(self.context.ctx).decode())
+
+    def collect(self, y, trajectory: int = 0):
+        """Store the pair (N, exact I^{ph-ph}) at the device state y (FP64 [n_y])."""
+        self._chk(load().rtbte_surrogate_collect(self.h, y.data_ptr(), trajectory))
+
+    def train(self, steps: int, batch: int, lr: float, horizon: int = 0) -> float:
+        """Adam steps on single pairs (horizon 0) or on differences of pairs of one trajectory
+        at most `horizon` collections apart; returns the last minibatch loss."""
+        loss = C.c_float()
+        self._chk(load().rtbte_surrogate_train(self.h, steps, batch, horizon, lr, C.byref(loss)))
+        return loss.value
+
+    def predict(self, y):
+        import torch
+
+        out = torch.empty_like(y)
+        self._chk(load().rtbte_surrogate_predict(self.h, y.data_ptr(), out.data_ptr()))
+        return out
+
+    @property
+    def num_params(self) -> int:
+        return int(load().rtbte_surrogate_num_params(self.h))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params, dtype=np.float32)
+        self._chk(load().rtbte_surrogate_get_params(self.h, out.ctypes.data))
+        return out
+
+    def set_params(self, flat: np.ndarray):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.num_params
+        self._chk(load().rtbte_surrogate_set_params(self.h, flat.ctypes.data))
+
+    def loss_grad(self, x: np.ndarray, t: np.ndarray):
+        """(loss, flat gradients, output) for normalised host batches x, t [B, ny, nx, C]."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        assert x.shape == t.shape and x.shape[1:] == (self.nq_s[1], self.nq_s[0], self.nmodes)
+        loss = C.c_float()
+        g = np.empty(self.num_params, dtype=np.float32)
+        out = np.empty_like(x)
+        self._chk(load().rtbte_surrogate_loss_grad(self.h, x.ctypes.data, t.ctypes.data, x.shape[0], C.byref(loss),
+                                                   g.ctypes.data, out.ctypes.data))
+        return loss.value, g, out
+
+    def stats(self):
+        mu, sd, so = (np.zeros(self.nmodes, dtype=np.float32) for _ in range(3))
+        n = C.c_int()
+        load().rtbte_surrogate_stats(self.h, mu.ctypes.data, sd.ctypes.data, so.ctypes.data, C.byref(n))
+        return mu, sd, so, n.value
+
+    def attach(self, judge_period: int = 10, judge_tol: float = 1e-2):
+        """Use this surrogate for the slow part of the context's MRI integrations."""
+        self._chk(load().rtbte_set_surrogate(self.context.ctx, self.h, judge_period, judge_tol))
+
+    def detach(self):
+        self._chk(load().rtbte_set_surrogate(self.context.ctx, None, 1, 1.0))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rtbte_surrogate_destroy(self.h)
+            self.h = None

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librtbte.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "builder.cu", "rhs.cu", "integrate.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "builder.cu", "rhs.cu", "integrate.cu", "noalloc.cu", "surrogate.cu"]
 HEADERS = ["internal.cuh", "rows.cuh"]
 
 

@@ -485,6 +485,7 @@ const char *rtbte_status_string(int s) {
 void rtbte_destroy(rtbte_ctx *ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    sur_orphan(ctx);
     destroy_graphs(ctx);
     for (auto &I : ctx->inst) {
         DevBuf *bufs[] = {&I.t_ek, &I.t_eps, &I.t_eid, &I.t_eidinv, &I.t_omega, &I.t_kmap, &I.t_lut, &I.t_g2,

@@ -671,13 +671,42 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
         StageArgs a = stage_args(ctx, Tf, cp, RTBTE_SLOW, nullptr);
         a.stage = -1;
         a.respect_done = 0;
+        // surrogate slow part (single instance): control variate about the last exact value,
+        // exact judge every sur_period slow steps, exact for the rest of the call once a judge fails
+        bool sur_on = ctx->sur != nullptr && NI == 1;
+        st->judge_err_max = -1.0;
+        if (sur_on) {  // surrogate values write the sub-lattice rows only; the slow part is 0 elsewhere
+            sur_reset(ctx);
+            RT_CUDA(ctx, cudaMemsetAsync(Fs, 0, sizeof(double) * 3 * n, ctx->stream));
+        }
+        auto slow_exact = [&](double *dst) -> int {
+            int r2;
+            if ((r2 = stage(ctx, a, ctx->stream))) return r2;
+            if ((r2 = launch_rhs_core(ctx, RTBTE_SLOW, nullptr, ctx->stream))) return r2;
+            if ((r2 = launch_rows(ctx, RTBTE_SLOW, dst, nullptr, ctx->stream))) return r2;
+            st->rhs_slow += NI;
+            st->slow_exact += NI;
+            return RTBTE_OK;
+        };
+        auto ycur = [&]() { return ctx->Y[ctx->ctl_host[0].cur].as<double>(); };
         for (long long k = 0; k < nsteps && !failed; ++k) {
             const double H = (k == nsteps - 1) ? t_out - t : o->h_s;
             // slow RHS at z_1 = y
-            if ((rc = stage(ctx, a, ctx->stream))) return rc;
-            if ((rc = launch_rhs_core(ctx, RTBTE_SLOW, nullptr, ctx->stream))) return rc;
-            if ((rc = launch_rows(ctx, RTBTE_SLOW, Fs, nullptr, ctx->stream))) return rc;
-            st->rhs_slow += NI;
+            if (!sur_on || k % ctx->sur_period == 0) {
+                if ((rc = slow_exact(Fs))) return rc;
+                if (sur_on) {
+                    double e = 0;
+                    if ((rc = sur_judge(ctx, ycur(), Fs, &e))) return rc;
+                    st->judge_err_max = std::max(st->judge_err_max, e);
+                    if (e > ctx->sur_tol) {
+                        sur_on = false;
+                        st->surrogate_fallbacks = 1;
+                    }
+                }
+            } else {
+                if ((rc = sur_value(ctx, ycur(), Fs))) return rc;
+                st->slow_surrogate++;
+            }
             for (int i = 1; i <= 3; ++i) {
                 const double dc = M.chat[i] - M.chat[i - 1];
                 const double ta = t + M.chat[i - 1] * H, tb = (i == 3) ? t + H : t + M.chat[i] * H;
@@ -697,10 +726,12 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
                     if (ctx->ctl_host[q].status != RTBTE_OK) failed = true;
                 if (failed) break;
                 if (i < 3) {
-                    if ((rc = stage(ctx, a, ctx->stream))) return rc;
-                    if ((rc = launch_rhs_core(ctx, RTBTE_SLOW, nullptr, ctx->stream))) return rc;
-                    if ((rc = launch_rows(ctx, RTBTE_SLOW, Fs + (long long)i * n, nullptr, ctx->stream))) return rc;
-                    st->rhs_slow += NI;
+                    if (sur_on) {
+                        if ((rc = sur_value(ctx, ycur(), Fs + (long long)i * n))) return rc;
+                        st->slow_surrogate++;
+                    } else if ((rc = slow_exact(Fs + (long long)i * n))) {
+                        return rc;
+                    }
                 }
             }
             if (failed) break;

@@ -200,6 +200,11 @@ struct rtbte_ctx {
     std::map<long long, cudaGraphExec_t> graphs;
     std::map<long long, int> graph_launches;  // kernels per replay of each graph
     long long launches = 0;
+    // surrogate of the slow part used by MRI integrations (not owned)
+    rtbte_surrogate *sur = nullptr;
+    std::vector<rtbte_surrogate *> surs;  // every live surrogate made on this context
+    int sur_period = 10;
+    double sur_tol = 1e-2;
     // collision-kernel timing (events recorded around launches outside graphs)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;            // free events
@@ -223,6 +228,13 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *opt, 
 void destroy_graphs(rtbte_ctx *ctx);
 // api.cu
 int fail(rtbte_ctx *ctx, int code, const std::string &msg);
+// Surrogate slow value (control variate about the last exact reference) at the device state y,
+// written to dst [n_y]; and the judge, which compares that value with the exact one and makes
+// (y, exact) the new reference (*relerr < 0 when there was no reference yet).
+int sur_value(rtbte_ctx *ctx, const double *y, double *dst);
+int sur_judge(rtbte_ctx *ctx, const double *y, const double *exact, double *relerr);
+void sur_reset(rtbte_ctx *ctx);  // forget the reference (the next judge only sets it)
+void sur_orphan(rtbte_ctx *ctx); // the context goes away: its surrogates refuse further work
 int cuda_fail(rtbte_ctx *ctx, cudaError_t e, const char *what);
 }  // namespace rtbte
 

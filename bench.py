@@ -83,7 +83,7 @@ def run_profile(args):
     ms, n = ctx.kernel_time()
     s = ctx.sizes(0)
     print(f"profile grid={args.grid} entries={s['eph_entries'] + s['phe_entries'] + s['pp_entries']} "
-          f"split_weight={w} rhs_kernel_avg_ms={ms / max(n, 1):.4f}", flush=True)
+          f"tuning={ctx.tuning()} rhs_kernel_avg_ms={ms / max(n, 1):.4f}", flush=True)
     ctx.close()
     return 0
 
@@ -599,7 +599,7 @@ def run_ours(args):
                                  "evaluation; populations are shared-memory staged by design" % (
                                      sz["channel_bytes"] / 1e9),
                            "channel_entries": entries, "replicas": world, "parallelism": f"replicas x{world}",
-                           "autotuned_split_weight": split_weight},
+                           "autotuned_split_weight": split_weight, "kernel_tuning": ctx.tuning()},
                 "sim_ps_per_s": sim_ps * world / (tmax / 1000.0), "rhs_evals_timed": tot_rhs,
                 "sim_ps_per_s_at_rel_err_1e-6": (max(acc["sim_ps_per_s_at_1e-6"].values())
                                                  if acc and acc["sim_ps_per_s_at_1e-6"] else None),

@@ -165,7 +165,7 @@ typedef struct rtbte_integ {
     int32_t max_nef;       /* consecutive error-test failures allowed (default 7)         */
     double safety, growth, growth_first, etamxf, etamin; /* 0: library defaults          */
     int32_t small_nef;     /* failures before etamxf applies (default 2)                  */
-    int32_t chunk;         /* attempts enqueued between host checks (0: auto)             */
+    int32_t chunk;         /* attempts per launch of the device attempt loop (0: 64)      */
 } rtbte_integ;
 
 typedef struct rtbte_stats {
@@ -208,8 +208,10 @@ int rtbte_upload_channels(rtbte_ctx *ctx, int inst, const rtbte_channels *ch);
 int rtbte_rhs(rtbte_ctx *ctx, double t, const double *y, double *ydot, unsigned parts);
 
 /* Advance the device state y (FP64 [n_y_total], caller-owned) from opt->t0 to t_out with
- * the method of `opt`.  All stepping, error norms and step-size control run on the device;
- * the host only checks a 4-byte flag between chunks of attempts.  On success y holds the
+ * the method of `opt`.  All stepping, error norms and step-size control run on the device:
+ * each integration span is one launch of a CUDA graph whose WHILE node repeats the attempt
+ * kernels until every instance is done (at most opt->chunk attempts per launch), and the host
+ * reads the status block once per launch.  On success y holds the
  * solution at t_out; on failure y holds the last accepted state and st->t its time.
  * Synchronises the stream.  Errors: INVALID_ARG, STATE, TOO_MANY_STEPS, STEP_UNDERFLOW,
  * ERR_TEST_FAIL, NONFINITE, CUDA. */
@@ -228,13 +230,20 @@ int rtbte_download_channels(rtbte_ctx *ctx, int inst, unsigned which, int64_t *o
 /* Set the stream used by later calls (cudaStream_t; NULL = default stream). */
 int rtbte_set_stream(rtbte_ctx *ctx, void *stream);
 
-/* Autotuner of the collision kernel's work split.  The persistent launch divides the work
- * items among CTAs by weight = entries + w per item, w being the fixed cost of an item in
- * entry equivalents; this call times the kernel for `parts` with several w and keeps the
- * fastest (returned in *chosen when not NULL).  Synchronises the stream; results of later
- * calls do not depend on the choice (rows add item partials in a fixed order).
+/* Autotuner of the collision kernel's launch.  The persistent launch divides the work items
+ * among CTAs by weight = (entries + w) x c_part per item, w being the fixed cost of an item in
+ * entry equivalents and c_part the calibrated cost of an entry of each part; a share s of the
+ * weight is split statically, the rest is taken in chunks by CTAs that finish early; each
+ * warp prefetches the entry arrays of the item d positions ahead of its sequence into L2.
+ * This call times the kernel for `parts` over candidates of w, c_part, d and s and keeps the
+ * fastest (w in *chosen when not NULL).  Synchronises the stream; results of later calls do
+ * not depend on the choice (rows add item partials in a fixed order).
  * Errors: INVALID_ARG, STATE, CUDA. */
 int rtbte_autotune(rtbte_ctx *ctx, unsigned parts, int *chosen);
+
+/* The launch parameters in use: w, d and s as described for rtbte_autotune (any pointer may be
+ * NULL).  Errors: INVALID_ARG. */
+int rtbte_get_tuning(const rtbte_ctx *ctx, int32_t *item_weight, int32_t *prefetch_items, double *static_share);
 
 /* Kernel timing.  While enabled, every launch of the collision kernel enqueued outside a
  * CUDA graph (rtbte_rhs and the first-step estimate) is bracketed by CUDA events recorded on

@@ -438,6 +438,14 @@ int rtbte_autotune(rtbte_ctx *ctx, unsigned parts, int *chosen) {
     return autotune(ctx, parts, chosen);
 }
 
+int rtbte_get_tuning(const rtbte_ctx *ctx, int32_t *item_weight, int32_t *prefetch_items, double *static_share) {
+    if (!ctx) return RTBTE_E_INVALID_ARG;
+    if (item_weight) *item_weight = ctx->item_overhead;
+    if (prefetch_items) *prefetch_items = ctx->pf_dist;
+    if (static_share) *static_share = ctx->static_frac;
+    return RTBTE_OK;
+}
+
 int rtbte_set_kernel_timing(rtbte_ctx *ctx, int enable) {
     if (!ctx) return RTBTE_E_INVALID_ARG;
     ctx->timing = enable != 0;
@@ -487,11 +495,16 @@ void rtbte_destroy(rtbte_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     sur_orphan(ctx);
     destroy_graphs(ctx);
+    ctx->loop_iter.release();
+    if (ctx->loop_iter_host) cudaFreeHost(ctx->loop_iter_host);
+    ctx->loop_iter_host = nullptr;
     for (auto &I : ctx->inst) {
         DevBuf *bufs[] = {&I.t_ek, &I.t_eps, &I.t_eid, &I.t_eidinv, &I.t_omega, &I.t_kmap, &I.t_lut, &I.t_g2,
                           &I.t_ppfull, &I.t_ppinv, &I.eph_idx, &I.eph_W, &I.phe_idx, &I.phe_W, &I.pp_idx, &I.pp_W};
         for (DevBuf *b : bufs) b->release();
     }
+    ctx->tail_tab.release();
+    ctx->tail_ctr.release();
     DevBuf *bufs[] = {&ctx->popf, &ctx->popN, &ctx->popP, &ctx->instdev, &ctx->compact, &ctx->items, &ctx->groups,
                       &ctx->partials, &ctx->eoff, &ctx->poff, &ctx->ppoff, &ctx->cta_tab, &ctx->wpre, &ctx->dyn_tab, &ctx->Y[0], &ctx->Y[1],
                       &ctx->K, &ctx->Fs, &ctx->forcing, &ctx->wrms_part, &ctx->ctl, &ctx->ystage, &ctx->ydstage};

@@ -10,8 +10,9 @@
 //   controller (one block): WRMS norm in a fixed order, accept if <= 1, PID step proposal
 //             h' = h eps_k^{-a1/p} eps_{k-1}^{+a2/p} eps_{k-2}^{-a3/p} (Eq. pid_controller)
 // Step size, time, error history and which of two state buffers is current live in device
-// memory, so the sequence is captured once into a CUDA graph and replayed; the host only
-// reads a small status block between chunks of attempts.  Readings of what the paper leaves
+// memory, so the sequence is captured once into a CUDA graph whose WHILE conditional node
+// repeats it on the device until every instance is done (at most a cap of attempts per
+// launch); the host reads a small status block once per launch.  Readings of what the paper leaves
 // open: PID signs alternate (ARKODE's documented form; the printed all-negative form is
 // pid_sign_mode 1), the other controller constants are ARKODE's documented defaults, the
 // first step follows Hairer-Norsett-Wanner's starting-step algorithm, and the MIS coupling
@@ -407,34 +408,91 @@ int enqueue_attempt(rtbte_ctx *ctx, const Tableau &T, const CtlParams &cp, unsig
     return RTBTE_OK;
 }
 
-long long graph_key(int method, unsigned parts, bool forcing, const CtlParams &cp) {
+long long graph_key(int method, unsigned parts, bool forcing, const CtlParams &cp, int cap) {
     // the controller constants are captured by value: key them by a hash of their bytes
-    unsigned long long h = 1469598103934665603ULL;
+    unsigned long long h = 1469598103934665603ULL ^ (unsigned long long)cap;
     const unsigned char *b = reinterpret_cast<const unsigned char *>(&cp);
     for (size_t i = 0; i < sizeof(cp); ++i) h = (h ^ b[i]) * 1099511628211ULL;
     return (long long)((h & ~0xffffULL) | ((unsigned long long)method << 8) | (parts << 1) | (forcing ? 1 : 0));
 }
 
-// One attempt as a CUDA graph (captured on the private stream, launched on the user stream).
-int attempt_graph(rtbte_ctx *ctx, int method, const CtlParams &cp, unsigned parts, const double *forcing,
+// Last node of the attempt loop's body: counts the attempts of this graph launch and keeps the
+// loop going while some instance is still integrating and fewer than `cap` attempts have run,
+// so the loop ends after at most `cap` attempts whatever the other kernels do.
+__global__ void loop_guard(const Ctl *ctl, int n_inst, int *iter, int cap, cudaGraphConditionalHandle h) {
+    __shared__ int active;
+    if (threadIdx.x == 0) active = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x)
+        if (!ctl[i].done) atomicExch(&active, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int it = *iter + 1;
+        *iter = it;
+        cudaGraphSetConditional(h, (active && it < cap) ? 1u : 0u);
+    }
+}
+
+// Attempts as one CUDA graph with a device-side loop: a memset zeroes the attempt counter, then
+// a WHILE conditional node runs [attempt kernels, loop_guard] until every instance is done or
+// `cap` attempts have run.  One launch (and one host check) per call instead of one per batch
+// of attempts.  Captured on the private stream, launched on the user stream.
+int attempt_graph(rtbte_ctx *ctx, int method, const CtlParams &cp, unsigned parts, const double *forcing, int cap,
                   cudaGraphExec_t *out, int *nlaunch) {
     const Tableau T = tableau_of(method);
-    long long key = graph_key(method, parts, forcing != nullptr, cp);
+    long long key = graph_key(method, parts, forcing != nullptr, cp, cap);
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
         *out = it->second;
         *nlaunch = ctx->graph_launches[key];
         return RTBTE_OK;
     }
+    if (!ctx->loop_iter.p) {
+        RT_CUDA(ctx, cudaMalloc(&ctx->loop_iter.p, 16));
+        ctx->loop_iter.bytes = 16;
+    }
+    if (!ctx->loop_iter_host) RT_CUDA(ctx, cudaMallocHost(&ctx->loop_iter_host, sizeof(int)));
+    int *iter = ctx->loop_iter.as<int>();
     cudaGraph_t g;
+    RT_CUDA(ctx, cudaGraphCreate(&g, 0));
+    auto bail = [&](cudaError_t e, const char *what) {
+        cudaGraphDestroy(g);
+        return cuda_fail(ctx, e, what);
+    };
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return bail(e, "cudaGraphConditionalHandleCreate");
+    cudaMemsetParams mp{};
+    mp.dst = iter;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = 1;
+    mp.height = 1;
+    mp.pitch = 4;
+    cudaGraphNode_t ms, cn;
+    if ((e = cudaGraphAddMemsetNode(&ms, g, nullptr, 0, &mp)) != cudaSuccess) return bail(e, "cudaGraphAddMemsetNode");
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&cn, g, &ms, nullptr, 1, &np)) != cudaSuccess) return bail(e, "cudaGraphAddNode");
+    cudaGraph_t body = np.conditional.phGraph_out[0];
     long long before = ctx->launches;
-    RT_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    e = cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bail(e, "cudaStreamBeginCaptureToGraph");
     int rc = enqueue_attempt(ctx, T, cp, parts, forcing, ctx->cap_stream);
-    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
-    ctx->graph_launches[key] = (int)(ctx->launches - before);  // kernels per replay
-    ctx->launches = before;                                   // captured, not executed
-    if (rc) return rc;
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    loop_guard<<<1, 256, 0, ctx->cap_stream>>>(ctx->ctl.as<Ctl>(), n_inst(ctx), iter, cap, h);
+    cudaError_t el = cudaGetLastError();
+    e = cudaStreamEndCapture(ctx->cap_stream, &body);
+    ctx->graph_launches[key] = (int)(ctx->launches - before) + 1;  // kernels per attempt, guard included
+    ctx->launches = before;                                       // captured, not executed
+    if (rc) {
+        cudaGraphDestroy(g);
+        return rc;
+    }
+    if (el != cudaSuccess) return bail(el, "loop_guard launch");
+    if (e != cudaSuccess) return bail(e, "cudaStreamEndCapture");
     cudaGraphExec_t ex;
     e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
@@ -474,18 +532,18 @@ long long sum_attempts(rtbte_ctx *ctx) {
 // Run attempts until every instance is done.  Returns a CUDA/launch error code, else RTBTE_OK
 // (the integration status of each instance is in ctx->ctl_host[i].status).  *attempts_out
 // receives the instance-attempts performed (one per active instance per attempt).
-int run_attempts(rtbte_ctx *ctx, int method, const CtlParams &cp, unsigned parts, const double *forcing, int chunk,
+int run_attempts(rtbte_ctx *ctx, int method, const CtlParams &cp, unsigned parts, const double *forcing, int cap,
                  long long *attempts_out) {
     cudaGraphExec_t ex;
     int nl, rc;
-    if ((rc = attempt_graph(ctx, method, cp, parts, forcing, &ex, &nl))) return rc;
+    if ((rc = attempt_graph(ctx, method, cp, parts, forcing, cap, &ex, &nl))) return rc;
     long long a0 = sum_attempts(ctx);
     for (;;) {
-        for (int k = 0; k < chunk; ++k) {
-            RT_CUDA(ctx, cudaGraphLaunch(ex, ctx->stream));
-            ctx->launches += nl;
-        }
+        RT_CUDA(ctx, cudaGraphLaunch(ex, ctx->stream));
+        RT_CUDA(ctx, cudaMemcpyAsync(ctx->loop_iter_host, ctx->loop_iter.p, sizeof(int), cudaMemcpyDeviceToHost,
+                                     ctx->stream));
         if ((rc = read_ctl(ctx))) return rc;
+        ctx->launches += (long long)*ctx->loop_iter_host * nl;
         if (all_done(ctx)) break;
     }
     if (attempts_out) *attempts_out = sum_attempts(ctx) - a0;
@@ -581,7 +639,7 @@ int fixed_rk4(rtbte_ctx *ctx, const rtbte_integ *o, unsigned parts, double t0, d
     }
     if ((rc = write_ctl(ctx))) return rc;
     CtlParams cp = ctl_params(o, 4);
-    return run_attempts(ctx, RTBTE_RK4, cp, parts, nullptr, o->chunk > 0 ? o->chunk : 8, attempts);
+    return run_attempts(ctx, RTBTE_RK4, cp, parts, nullptr, o->chunk > 0 ? o->chunk : kLoopCap, attempts);
 }
 
 // Aggregate per-instance controller counters into the call's statistics.
@@ -648,7 +706,7 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
             ctx->launches++;
         }
         long long att = 0;
-        if ((rc = run_attempts(ctx, m, cp, RTBTE_ALL, nullptr, o->chunk > 0 ? o->chunk : 8, &att))) return rc;
+        if ((rc = run_attempts(ctx, m, cp, RTBTE_ALL, nullptr, o->chunk > 0 ? o->chunk : kLoopCap, &att))) return rc;
         st->attempts = att;
         st->rhs_full = att * T.S + (est ? 2LL * NI : 0);
         gather_stats(ctx, st, false);
@@ -720,7 +778,7 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
                     first_inner = false;
                 }
                 long long att = 0;
-                if ((rc = run_attempts(ctx, fm, cp, RTBTE_FAST, r, o->chunk > 0 ? o->chunk : 4, &att))) return rc;
+                if ((rc = run_attempts(ctx, fm, cp, RTBTE_FAST, r, o->chunk > 0 ? o->chunk : kLoopCap, &att))) return rc;
                 inner_attempts += att;
                 for (int q = 0; q < NI; ++q)
                     if (ctx->ctl_host[q].status != RTBTE_OK) failed = true;

@@ -34,8 +34,14 @@ constexpr int kRhsThreads = 512;
 constexpr int kMaxModes = 16;
 constexpr int kMaxStages = 5;
 constexpr int kWrmsBlocks = 512;
+constexpr int kLoopCap = 64;     // attempts per launch of an attempt-loop graph (default)
 
 enum { PART_EPH = 0, PART_PHE = 1, PART_PP = 2 };
+// Lanes working on one item: an item holds at most 16 x kItemLanes entries and a warp works on
+// 32 / kItemLanes items at a time (16 and 8 lanes, which pack short segments together, measured
+// slower on the graphene-like workload than whole-warp items).
+constexpr int kItemLanes = 32;
+
 
 struct __align__(16) Item {
     long long begin;      // first entry, relative to the group's entry arrays
@@ -188,7 +194,12 @@ struct rtbte_ctx {
     int part_first[3] = {0, 0, 0};
     int grid = 0, threads = rtbte::kRhsThreads;
     std::vector<unsigned short> item_len_h;  // entries per work item (host copy for re-splitting)
+    std::vector<int> group_begin_h;          // first item of each group (host copy)
     int item_overhead = 320;                 // work-split weight of an item beyond its entries
+    double static_frac = 1.0;                // share of the weight split statically (rest: dynamic chunks)
+    int pf_dist = 3;                         // collision kernel: L2 prefetch distance in items
+    rtbte::DevBuf tail_tab, tail_ctr;        // dynamic chunks {first, end, group, 0} per mask; grab/exit counters
+    int tail_off[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // chunks of mask m: [tail_off[m-1], tail_off[m])
     double part_scale[3] = {1.0, 1.0, 1.0};  // relative cost of an entry of each part
     size_t smem_bytes = 0;
     bool staged = false;
@@ -198,7 +209,9 @@ struct rtbte_ctx {
     rtbte::DevBuf Y[2], K, Fs, forcing, wrms_part, ctl, ystage, ydstage;  // wrms_part: 2 x n_y squared norms
     rtbte::Ctl *ctl_host = nullptr;  // pinned mirror of the per-instance controllers
     std::map<long long, cudaGraphExec_t> graphs;
-    std::map<long long, int> graph_launches;  // kernels per replay of each graph
+    std::map<long long, int> graph_launches;  // kernels per attempt of each attempt-loop graph
+    rtbte::DevBuf loop_iter;                  // attempts run by the last attempt-loop launch (device)
+    int *loop_iter_host = nullptr;            // pinned mirror
     long long launches = 0;
     // surrogate of the slow part used by MRI integrations (not owned)
     rtbte_surrogate *sur = nullptr;

@@ -6,9 +6,11 @@
 // staged per CTA in shared memory: the instance's electron occupations f plus, for e-ph
 // work, the occupations N of one phonon mode (the e-ph lists are blocked by mode for this
 // reason); for ph-e work only f; for ph-ph work the sub-lattice N.  Each warp owns one
-// work item (<= 512 entries of a single destination segment) and reduces it with a
-// compensated (two-sum) accumulation and a compensated warp-shuffle tree; the partial is
-// written per item, and the row kernels add partials in item order (deterministic).
+// work item (<= 512 entries of a single destination segment), accumulates it per lane with
+// compensated (two-sum) additions and adds the lanes with a shuffle tree; the partial is
+// written per item, and the row kernels add partials in item order (deterministic).  CTAs
+// first run a static share of the items (split by estimated cost), then take the rest in
+// chunks from a counter; warps may prefetch upcoming items' entries into L2.
 //
 // Per-entry arithmetic uses the exact algebraic reductions of the paper's factors
 // (Methods A):  F_em = f(1-f') + N(f-f'),  F_abs = N(f-f') - f'(1-f),
@@ -40,29 +42,19 @@ template <class R> __device__ __forceinline__ void two_sum(R &s, R &c, R x) {
     c += e;
 }
 
-// Compensated butterfly reduction; every lane ends with the same bits.
-template <class R> __device__ __forceinline__ void warp_reduce2(R &s, R &c) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        R s2 = __shfl_xor_sync(kFull, s, o);
-        R c2 = __shfl_xor_sync(kFull, c, o);
-        R t = s + s2;
-        R bp = t - s;
-        R e = (s - (t - bp)) + (s2 - bp);
-        s = t;
-        c = (c + c2) + e;
-    }
-}
-
 struct KParams {
     const Item *items;
     const Group *groups;
     int n_groups;
-    const int *cta_items;  // [grid+1] first item of each CTA's range (real item indices)
+    const int *cta_items;  // [grid+1] first item of each CTA's static range (real item indices)
     unsigned mask;         // parts evaluated (groups of other parts are skipped)
     void *partials;
     const void *popf, *popN, *popP;
     const Ctl *ctl;  // per-instance controllers: launches inside an integrator skip finished instances
+    const int4 *tail;  // dynamic chunks {first item, end item, group, 0} after the static ranges
+    int n_tail;
+    int *tail_ctr;     // [0] next chunk to take, [1] CTAs finished (reset by the last one)
+    int pf_dist;       // L2 prefetch distance in items of a warp's sequence (0: off)
 };
 
 template <class R>
@@ -84,18 +76,21 @@ template <class R> struct GroupView {
     int part, sb, pb;
 };
 
-// Entry loads of one item: 4 vectors of 4 entries per lane (16-byte streaming loads).
-template <class R> struct Batch;
-template <> struct Batch<float> {
-    uint4 iv[4];
-    float4 wv[4];
-    __device__ __forceinline__ void issue(const GroupView<float> &V, const Item &it, int lane) {
+// Entry loads of one item on a sub-warp of SW lanes: VPL vectors of 4 entries per lane
+// (16-byte streaming loads); sl is the lane's index in its sub-warp.
+template <class R, int VPL, int SW> struct Batch;
+template <int VPL, int SW> struct Batch<float, VPL, SW> {
+    uint4 iv[VPL];
+    float4 wv[VPL];
+    float Np;  // ph-e destination population, loaded with the entries
+    __device__ __forceinline__ void issue(const GroupView<float> &V, const Item &it, int sl) {
         const int nv = it.len >> 2;
+        if (V.part == PART_PHE) Np = V.Nglob[it.dest];
         const uint4 *ip = reinterpret_cast<const uint4 *>(V.idx + it.begin);
         const float4 *wp = reinterpret_cast<const float4 *>(V.W + it.begin);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int v = lane + 32 * j;
+        for (int j = 0; j < VPL; ++j) {
+            const int v = sl + SW * j;
             if (v < nv) {
                 iv[j] = __ldcs(ip + v);
                 wv[j] = __ldcs(wp + v);
@@ -106,16 +101,18 @@ template <> struct Batch<float> {
         return k == 0 ? wv[j].x : k == 1 ? wv[j].y : k == 2 ? wv[j].z : wv[j].w;
     }
 };
-template <> struct Batch<double> {
-    uint4 iv[4];
-    double2 wa[4], wb[4];
-    __device__ __forceinline__ void issue(const GroupView<double> &V, const Item &it, int lane) {
+template <int VPL, int SW> struct Batch<double, VPL, SW> {
+    uint4 iv[VPL];
+    double2 wa[VPL], wb[VPL];
+    double Np;  // ph-e destination population, loaded with the entries
+    __device__ __forceinline__ void issue(const GroupView<double> &V, const Item &it, int sl) {
         const int nv = it.len >> 2;
+        if (V.part == PART_PHE) Np = V.Nglob[it.dest];
         const uint4 *ip = reinterpret_cast<const uint4 *>(V.idx + it.begin);
         const double2 *wp = reinterpret_cast<const double2 *>(V.W + it.begin);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int v = lane + 32 * j;
+        for (int j = 0; j < VPL; ++j) {
+            const int v = sl + SW * j;
             if (v < nv) {
                 iv[j] = __ldcs(ip + v);
                 wa[j] = __ldcs(wp + 2 * v);
@@ -132,10 +129,11 @@ __device__ __forceinline__ unsigned comp4(const uint4 &e, int k) {
     return k == 0 ? e.x : k == 1 ? e.y : k == 2 ? e.z : e.w;
 }
 
-// Sum of W*F over one item: each 4-entry vector is summed with an FMA chain and the vector
-// sums are added with two-sum; the warp then reduces (hi, lo) with compensation.
-template <class R>
-__device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &it, const Batch<R> &b, int lane,
+// Per-lane sum of W*F over one item: each 4-entry vector is summed with an FMA chain and the
+// vector sums are added with two-sum into (acc, cmp); the warp reduction is done later for
+// four items at once (Pending).
+template <class R, int VPL, int SW>
+__device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &it, const Batch<R, VPL, SW> &b, int sl,
                                              R &acc, R &cmp) {
     const int nv = it.len >> 2;
     acc = R(0);
@@ -145,8 +143,8 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
         const R fd = V.s0[it.dest];
         if (it.proc == 0) {  // F_em = f(1-f') + N(f-f') = fma(N, f-f', fma(f', -f, f))
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (lane + 32 * j >= nv) continue;
+            for (int j = 0; j < VPL; ++j) {
+                if (sl + SW * j >= nv) continue;
                 R t = R(0);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -160,8 +158,8 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
         } else {  // F_abs = N(f-f') - f'(1-f)
             const R u = R(1) - fd;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (lane + 32 * j >= nv) continue;
+            for (int j = 0; j < VPL; ++j) {
+                if (sl + SW * j >= nv) continue;
                 R t = R(0);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -175,10 +173,10 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
         }
     } else if (V.part == PART_PHE) {  // F_abs(f_d, f_s, N_p) with N_p per item
         const unsigned smask = (1u << V.sb) - 1u;
-        const R Np = V.Nglob[it.dest];
+        const R Np = b.Np;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (lane + 32 * j >= nv) continue;
+        for (int j = 0; j < VPL; ++j) {
+            if (sl + SW * j >= nv) continue;
             R t = R(0);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -194,8 +192,8 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
         const R Na = V.s0[it.dest];
         if (it.proc == 0) {  // G_em = N(N'+N''+1) - N'N''
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (lane + 32 * j >= nv) continue;
+            for (int j = 0; j < VPL; ++j) {
+                if (sl + SW * j >= nv) continue;
                 R t = R(0);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -208,8 +206,8 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
             }
         } else {  // G_abs = N(N''-N') - N'(N''+1)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (lane + 32 * j >= nv) continue;
+            for (int j = 0; j < VPL; ++j) {
+                if (sl + SW * j >= nv) continue;
                 R t = R(0);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -221,16 +219,6 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
                 two_sum(acc, cmp, t);
             }
         }
-    }
-    warp_reduce2(acc, cmp);
-}
-
-template <class R>
-__device__ __forceinline__ void store_partial(const KParams &P, int iid, R acc, R cmp, int lane) {
-    if (lane == 0) {
-        R *out = reinterpret_cast<R *>(P.partials) + 2LL * iid;
-        out[0] = acc;
-        out[1] = cmp;
     }
 }
 
@@ -276,96 +264,219 @@ struct DescStream {
         d.w = __shfl_sync(kFull, cur.w, src);
         return item_from(d);
     }
+    // descriptor of item kb + h*stride for this lane (h = its sub-warp), kb warp-uniform and
+    // advancing by (items per iteration) * stride per call
+    __device__ __forceinline__ Item get_sub(int kb, int h) {
+        if (kb - k0 >= 32 * stride) {
+            k0 += 32 * stride;
+            cur = nxt;
+            nxt = fetch(k0 + 32 * stride, threadIdx.x & 31);
+        }
+        const int off = (kb - k0) / stride + h;
+        const bool in_cur = off < 32;
+        const int src = in_cur ? off : off - 32;
+        int4 d;
+        d.x = __shfl_sync(kFull, in_cur ? cur.x : nxt.x, src);
+        d.y = __shfl_sync(kFull, in_cur ? cur.y : nxt.y, src);
+        d.z = __shfl_sync(kFull, in_cur ? cur.z : nxt.z, src);
+        d.w = __shfl_sync(kFull, in_cur ? cur.w : nxt.w, src);
+        return item_from(d);
+    }
+    // descriptor of item k in the current or next block, without advancing (warp-uniform k)
+    __device__ __forceinline__ Item peek(int k) const {
+        const int off = (k - k0) / stride;
+        const bool in_cur = off < 32;
+        const int src = in_cur ? off : off - 32;
+        int4 d;
+        d.x = __shfl_sync(kFull, in_cur ? cur.x : nxt.x, src);
+        d.y = __shfl_sync(kFull, in_cur ? cur.y : nxt.y, src);
+        d.z = __shfl_sync(kFull, in_cur ? cur.z : nxt.z, src);
+        d.w = __shfl_sync(kFull, in_cur ? cur.w : nxt.w, src);
+        return item_from(d);
+    }
 };
 
-// Items a, a+st, a+2st, ... < b of one group for one warp.  With PIPE, the next item's entry
-// loads are in flight while the current item is computed (two register buffers).
-template <class R, bool PIPE>
-__device__ __forceinline__ void run_range(const KParams &P, const GroupView<R> &V, int a, int b, int st, int lane) {
-    if (a >= b) return;
-    DescStream D;
-    D.init(P.items, a, b, st, lane);
-    R acc, cmp;
-    if (!PIPE) {
-        for (int k = a; k < b; k += st) {
-            const Item it = D.get(k, lane);
-            Batch<R> B;
-            B.issue(V, it, lane);
-            compute_item(V, it, B, lane, acc, cmp);
-            store_partial(P, k, acc, cmp, lane);
-        }
-        return;
-    }
-    Batch<R> A, B;
-    int k = a;
-    Item ia = D.get(k, lane);
-    A.issue(V, ia, lane);
-    for (;;) {
-        const bool hb = k + st < b;
-        Item ib;
-        if (hb) {
-            ib = D.get(k + st, lane);
-            B.issue(V, ib, lane);
-        }
-        compute_item(V, ia, A, lane, acc, cmp);
-        store_partial(P, k, acc, cmp, lane);
-        if (!hb) break;
-        k += st;
-        const bool ha = k + st < b;
-        if (ha) {
-            ia = D.get(k + st, lane);
-            A.issue(V, ia, lane);
-        }
-        compute_item(V, ib, B, lane, acc, cmp);
-        store_partial(P, k, acc, cmp, lane);
-        if (!ha) break;
-        k += st;
+// L2 prefetch of item k's entry arrays (one bulk prefetch per array, issued by lane 0), so
+// that its streaming loads, issued `dist` items later, find the lines in L2.  Warp-uniform k.
+template <class R>
+__device__ __forceinline__ void prefetch_item(const GroupView<R> &V, const DescStream &D, int k, int b, int lane) {
+    if (k >= b || k - D.k0 >= 64 * D.stride) return;
+    const Item it = D.peek(k);
+    if (lane == 0 && it.len > 0) {
+        const uint32_t *ip = V.idx + it.begin;
+        const R *wp = V.W + it.begin;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(ip), "r"((unsigned)it.len * 4u) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(wp), "r"((unsigned)(it.len * sizeof(R)))
+                     : "memory");
     }
 }
 
-template <class R, bool STAGED, bool PIPE, int MINB>
-__global__ void __launch_bounds__(kRhsThreads, MINB) rhs_kernel(KParams P) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *sm = reinterpret_cast<R *>(smem_raw);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int ra = P.cta_items[blockIdx.x], rb = P.cta_items[blockIdx.x + 1];
-    if (ra >= rb) return;
-    int lo = 0, hi = P.n_groups - 1;  // last group with item_begin <= ra
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (P.groups[mid].item_begin <= ra) lo = mid; else hi = mid - 1;
+// Item sum: the lane's compensated sum (acc + cmp) is rounded once, then added over the
+// sub-warp by a butterfly in a fixed order (every lane ends with the same bits).  The RHS error
+// is set by the conversion of the populations to FP32 (about 5e-8 relative on the parity
+// models), not by this tree: the compensated tree measured the same to two digits.
+template <class R, int SW>
+__device__ __forceinline__ void finish_item(const KParams &P, int k, bool valid, R acc, R cmp, int sl) {
+    acc += cmp;
+    cmp = R(0);
+#pragma unroll
+    for (int o = SW / 2; o; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if (sl == 0 && valid) {
+        R *out = reinterpret_cast<R *>(P.partials) + 2LL * k;
+        out[0] = acc;
+        out[1] = cmp;
     }
-    for (int g = lo; g < P.n_groups; ++g) {
-        const Group &G = P.groups[g];
-        const int gb = G.item_begin, ge = G.item_end;
-        if (gb >= rb) break;
-        if (max(ra, gb) >= min(rb, ge)) continue;
-        if (!(P.mask & (1u << G.part))) continue;
-        if (P.ctl && P.ctl[G.inst].done) continue;  // instance already at its t_out
-        GroupView<R> V;
-        V.idx = G.idx;
-        V.W = reinterpret_cast<const R *>(G.W);
-        V.part = G.part;
-        V.sb = G.s_bits;
-        V.pb = G.pp_bits;
-        V.Nglob = reinterpret_cast<const R *>(P.popN) + G.N_inst;
-        const R *src0 = reinterpret_cast<const R *>(G.part == PART_PP ? P.popP : P.popf) + G.stage0_src;
-        const R *src1 = reinterpret_cast<const R *>(P.popN) + G.stage1_src;
-        if (STAGED) {
-            const int l0 = G.stage0_len, l1 = G.stage1_len;
+}
+
+// Items a, a+st, a+2st, ... < b of one group for one warp.  The warp works on 32/SW items at
+// a time, one per sub-warp of SW lanes (items of the part are cut to at most 16*SW entries:
+// short ph-e segments pack four to a warp).  With PIPE, the next items' entry loads are in
+// flight while the current ones are computed (two register buffers).
+template <class R, bool PIPE, int SW>
+__device__ __forceinline__ void run_range(const KParams &P, const GroupView<R> &V, int a, int b, int st, int lane) {
+    if (a >= b) return;
+    constexpr int G = 32 / SW;
+    const int h = lane / SW, sl = lane & (SW - 1);
+    DescStream D;
+    D.init(P.items, a, b, st, lane);
+    auto next = [&](int kb) { return G == 1 ? D.get(kb, lane) : D.get_sub(kb, h); };
+    auto valid = [&](int kb) { return G == 1 || kb + h * st < b; };
+    const int pf = P.pf_dist;  // iterations ahead whose entries are prefetched into L2 (0: none)
+    R acc, cmp;
+    if (pf > 0)
+        for (int j = 1; j < pf; ++j) prefetch_item(V, D, a + j * G * st, b, lane);
+    if (!PIPE) {
+        for (int k = a; k < b; k += G * st) {
+            const Item it = next(k);
+            if (pf > 0) prefetch_item(V, D, k + pf * G * st, b, lane);
+            Batch<R, 4, SW> B;
+            B.issue(V, it, sl);
+            compute_item<R, 4, SW>(V, it, B, sl, acc, cmp);
+            finish_item<R, SW>(P, k + h * st, valid(k), acc, cmp, sl);
+        }
+        return;
+    }
+    Batch<R, 4, SW> A, B;
+    int k = a;
+    Item ia = next(k);
+    A.issue(V, ia, sl);
+    for (;;) {
+        const bool hb = k + G * st < b;
+        Item ib;
+        if (hb) {
+            ib = next(k + G * st);
+            B.issue(V, ib, sl);
+        }
+        if (pf > 0) prefetch_item(V, D, k + pf * G * st, b, lane);
+        compute_item<R, 4, SW>(V, ia, A, sl, acc, cmp);
+        finish_item<R, SW>(P, k + h * st, valid(k), acc, cmp, sl);
+        if (!hb) break;
+        k += G * st;
+        const bool ha = k + G * st < b;
+        if (ha) {
+            ia = next(k + G * st);
+            A.issue(V, ia, sl);
+        }
+        if (pf > 0) prefetch_item(V, D, k + pf * G * st, b, lane);
+        compute_item<R, 4, SW>(V, ib, B, sl, acc, cmp);
+        finish_item<R, SW>(P, k + h * st, valid(k), acc, cmp, sl);
+        if (!ha) break;
+        k += G * st;
+    }
+}
+
+// Point V at group g's populations, staging them in shared memory unless this CTA already
+// holds them (`staged` is the group currently in shared memory).  Called by all threads.
+template <class R, bool STAGED>
+__device__ __forceinline__ void enter_group(const KParams &P, int g, R *sm, int &staged, GroupView<R> &V) {
+    const Group &G = P.groups[g];
+    V.idx = G.idx;
+    V.W = reinterpret_cast<const R *>(G.W);
+    V.part = G.part;
+    V.sb = G.s_bits;
+    V.pb = G.pp_bits;
+    V.Nglob = reinterpret_cast<const R *>(P.popN) + G.N_inst;
+    const R *src0 = reinterpret_cast<const R *>(G.part == PART_PP ? P.popP : P.popf) + G.stage0_src;
+    const R *src1 = reinterpret_cast<const R *>(P.popN) + G.stage1_src;
+    if (STAGED) {
+        const int l0 = G.stage0_len, l1 = G.stage1_len;
+        if (staged != g) {
             __syncthreads();  // the previous group's readers are done with the buffer
             stage_copy<R>(sm, src0, l0);
             if (l1 > 0) stage_copy<R>(sm + l0, src1, l1);
             asm volatile("cp.async.commit_group;\n" ::: "memory");
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
             __syncthreads();
-            V.s0 = sm;
-            V.s1 = sm + l0;
-        } else {
-            V.s0 = src0;
-            V.s1 = src1;
+            staged = g;
         }
-        run_range<R, PIPE>(P, V, max(ra, gb) + warp, min(rb, ge), nwarps, lane);
+        V.s0 = sm;
+        V.s1 = sm + l0;
+    } else {
+        V.s0 = src0;
+        V.s1 = src1;
+    }
+}
+
+// Persistent collision kernel.  Each CTA first runs its static range of items (cta_items,
+// split by estimated cost), then takes dynamic chunks of the remaining items from a shared
+// counter until none is left, so that SMs that finish early absorb the tail of the work.
+// Items are round-robin over the warps of the CTA; every item writes its own partial, so the
+// result does not depend on which CTA ran it.
+template <class R, bool STAGED, bool PIPE, int MINB>
+__global__ void __launch_bounds__(kRhsThreads, MINB) rhs_kernel(KParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_chunk;
+    R *sm = reinterpret_cast<R *>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int staged = -1;
+    const int ra = P.cta_items[blockIdx.x], rb = P.cta_items[blockIdx.x + 1];
+    int g = P.n_groups;  // next group of the static range
+    if (ra < rb) {
+        int lo = 0, hi = P.n_groups - 1;  // last group with item_begin <= ra
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (P.groups[mid].item_begin <= ra) lo = mid; else hi = mid - 1;
+        }
+        g = lo;
+    }
+    bool dynamic = false;
+    for (;;) {
+        int ug, ua, ub;  // next unit of work: items [ua, ub) of group ug
+        if (!dynamic) {
+            if (g >= P.n_groups || P.groups[g].item_begin >= rb) {
+                dynamic = true;
+                if (P.n_tail == 0) break;
+                continue;
+            }
+            ug = g++;
+            ua = max(ra, P.groups[ug].item_begin);
+            ub = min(rb, P.groups[ug].item_end);
+            if (ua >= ub) continue;
+        } else {
+            __syncthreads();  // every warp is done with the previous unit and with s_chunk
+            if (threadIdx.x == 0) s_chunk = atomicAdd(P.tail_ctr, 1);
+            __syncthreads();
+            const int c = s_chunk;
+            if (c >= P.n_tail) break;
+            const int4 ch = P.tail[c];
+            ug = ch.z;
+            ua = ch.x;
+            ub = ch.y;
+        }
+        const Group &G = P.groups[ug];
+        if (!(P.mask & (1u << G.part))) continue;
+        if (P.ctl && P.ctl[G.inst].done) continue;  // instance already at its t_out
+        GroupView<R> V;
+        enter_group<R, STAGED>(P, ug, sm, staged, V);
+        run_range<R, PIPE, kItemLanes>(P, V, ua + warp, ub, nwarps, lane);
+    }
+    if (dynamic && P.n_tail > 0 && threadIdx.x == 0) {  // the last CTA out resets the counters
+        __threadfence();
+        if (atomicAdd(P.tail_ctr + 1, 1) == (int)gridDim.x - 1) {
+            P.tail_ctr[0] = 0;
+            P.tail_ctr[1] = 0;
+            __threadfence();
+        }
     }
 }
 
@@ -462,10 +573,11 @@ RowParams row_params(rtbte_ctx *ctx) {
     return Q;
 }
 
-// Per-mask work split of the persistent grid: CTA c owns the virtual items [t[c], t[c+1]) of
-// equal weight, weight = entries + `overhead` per item (the fixed cost of an item in entry
-// equivalents); stored as [grid][nwarps+1] virtual starts (warp columns split the CTA range
-// by the same weights).
+// Per-mask work split of the persistent grid.  Item weight = (entries + `overhead`) x the
+// part's calibrated cost per entry.  The first `static_frac` of a mask's weight is split into
+// equal-weight contiguous CTA ranges (table [mask][grid+1] of real item indices); the rest is
+// cut into dynamic chunks of decreasing weight (half the remaining weight per grid, at least
+// 1/40 of a CTA's share, never across a group boundary), taken by CTAs in order at run time.
 int split_tables(rtbte_ctx *ctx, int overhead) {
     const int G = ctx->grid;
     const std::vector<unsigned short> &len = ctx->item_len_h;
@@ -478,7 +590,13 @@ int split_tables(rtbte_ctx *ctx, int overhead) {
             wpre[k + 1] = sc * (len[k] + overhead);
     }
     for (int k = 0; k < n; ++k) wpre[k + 1] += wpre[k];
+    std::vector<int> item_group(n, 0);
+    for (size_t g = 0; g < ctx->group_begin_h.size(); ++g) {
+        const int e = g + 1 < ctx->group_begin_h.size() ? ctx->group_begin_h[g + 1] : n;
+        for (int k = ctx->group_begin_h[g]; k < e; ++k) item_group[k] = (int)g;
+    }
     std::vector<int> tab(7LL * (G + 1), 0);
+    std::vector<int4> tail;
     std::vector<long long> apre;  // prefix of the enabled parts' weights, item order
     std::vector<int> aidx;
     for (unsigned mask = 1; mask <= 7; ++mask) {
@@ -493,6 +611,8 @@ int split_tables(rtbte_ctx *ctx, int overhead) {
         }
         const long long total = apre.back();
         const int na = (int)aidx.size();
+        const long long split = ctx->static_frac >= 1.0 ? total : (long long)(ctx->static_frac * (double)total);
+        const int js = (int)(std::lower_bound(apre.begin(), apre.end(), split) - apre.begin());  // first tail item
         int *t = tab.data() + (long long)(mask - 1) * (G + 1);
         for (int c = 0; c <= G; ++c) {
             if (na == 0) {
@@ -500,17 +620,31 @@ int split_tables(rtbte_ctx *ctx, int overhead) {
                 continue;
             }
             if (c == G) {
-                t[c] = n;
+                t[c] = js >= na ? n : aidx[js];
                 continue;
             }
-            const long long target = total * c / G;
+            const long long target = split * c / G;
             const int j = (int)(std::lower_bound(apre.begin(), apre.end(), target) - apre.begin());
-            t[c] = c == 0 ? 0 : (j >= na ? n : aidx[j]);
+            t[c] = c == 0 ? 0 : (j >= na ? n : (j >= js ? aidx[js] : aidx[j]));
         }
+        const long long wmin = std::max<long long>(1, total / (40LL * G));
+        for (int j = js; j < na;) {
+            const long long remaining = total - apre[j];
+            const long long want = std::max(wmin, remaining / (2LL * G));
+            const int g = item_group[aidx[j]];
+            int j2 = j + 1;
+            while (j2 < na && item_group[aidx[j2]] == g && aidx[j2] == aidx[j2 - 1] + 1 && apre[j2] - apre[j] < want)
+                ++j2;
+            tail.push_back(make_int4(aidx[j], aidx[j2 - 1] + 1, g, 0));
+            j = j2;
+        }
+        ctx->tail_off[mask] = (int)tail.size();
     }
     ctx->item_overhead = overhead;
     int rc;
     if ((rc = upload_vec(ctx, ctx->wpre, wpre))) return rc;
+    if (tail.empty()) tail.push_back(make_int4(0, 0, 0, 0));
+    if ((rc = upload_vec(ctx, ctx->tail_tab, tail))) return rc;
     return upload_vec(ctx, ctx->cta_tab, tab);
 }
 
@@ -521,12 +655,13 @@ int make_plan(rtbte_ctx *ctx) {
     std::vector<Group> groups;
     std::vector<int> eoff, poff, ppoff;
     std::vector<InstDev> idev(ctx->inst.size());
+    const int cut = 16 * kItemLanes;  // entries per item at most
     auto add_seg = [&](long long b, long long e, int dest, int proc) {
-        for (long long x = b; x < e; x += kItemEntries) {
+        for (long long x = b; x < e; x += cut) {
             Item it;
             it.begin = x;
             it.dest = dest;
-            it.len = (unsigned short)std::min<long long>(kItemEntries, e - x);
+            it.len = (unsigned short)std::min<long long>(cut, e - x);
             it.proc = (unsigned char)proc;
             it.pad = 0;
             items.push_back(it);
@@ -557,6 +692,7 @@ int make_plan(rtbte_ctx *ctx) {
             for (int d = 0; d < I.d.n_c; ++d) {
                 eoff.push_back((int)items.size());
                 long long g = ((long long)nu * I.d.n_c + d) * 2;
+                
                 add_seg(I.eph_off[g], I.eph_off[g + 1], d, 0);
                 add_seg(I.eph_off[g + 1], I.eph_off[g + 2], d, 1);
             }
@@ -589,6 +725,7 @@ int make_plan(rtbte_ctx *ctx) {
             poff.push_back((int)items.size());
             int nu = (int)(p / I.N_q);
             long long q = p - (long long)nu * I.N_q;
+            
             add_seg(I.phe_off[p], I.phe_off[p + 1], (int)((long long)nu * I.N_q_pad + q), 1);
         }
         poff.push_back((int)items.size());
@@ -617,6 +754,7 @@ int make_plan(rtbte_ctx *ctx) {
         G.P_inst = I.P_off;
         for (long long a = 0; a < I.M; ++a) {
             ppoff.push_back((int)items.size());
+            
             add_seg(I.pp_off[2 * a], I.pp_off[2 * a + 1], (int)a, 0);
             add_seg(I.pp_off[2 * a + 1], I.pp_off[2 * a + 2], (int)a, 1);
         }
@@ -649,12 +787,19 @@ int make_plan(rtbte_ctx *ctx) {
         compact.insert(compact.end(), I.compact.begin(), I.compact.end());
     }
     // staging decision and launch shape
-    ctx->staged = max_stage <= ctx->smem_optin;
+    ctx->staged = max_stage + 64 <= ctx->smem_optin;  // 64 B left for the kernel's static shared memory
     ctx->smem_bytes = ctx->staged ? std::max<size_t>(max_stage, 16) : 0;
     ctx->grid = ctx->num_sms * (ctx->staged ? 1 : 2);
     ctx->item_len_h.resize(items.size());
     for (size_t k = 0; k < items.size(); ++k) ctx->item_len_h[k] = items[k].len;
+    ctx->group_begin_h.resize(groups.size());
+    for (size_t g = 0; g < groups.size(); ++g) ctx->group_begin_h[g] = groups[g].item_begin;
     int rc;
+    if (!ctx->tail_ctr.p) {
+        RT_CUDA(ctx, cudaMalloc(&ctx->tail_ctr.p, 16));
+        ctx->tail_ctr.bytes = 16;
+        RT_CUDA(ctx, cudaMemsetAsync(ctx->tail_ctr.p, 0, 16, ctx->stream));
+    }
     if ((rc = upload_vec(ctx, ctx->items, items))) return rc;
     if ((rc = upload_vec(ctx, ctx->groups, groups))) return rc;
     if ((rc = upload_vec(ctx, ctx->eoff, eoff))) return rc;
@@ -675,11 +820,11 @@ int make_plan(rtbte_ctx *ctx) {
     RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (ctx->staged) {
         if (ctx->precision == RTBTE_PREC_FP64)
-            RT_CUDA(ctx, cudaFuncSetAttribute(rhs_kernel<double, true, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)ctx->smem_bytes));
+            RT_CUDA(ctx, cudaFuncSetAttribute(rhs_kernel<double, true, false, 1>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_bytes));
         else
-            RT_CUDA(ctx, cudaFuncSetAttribute(rhs_kernel<float, true, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)ctx->smem_bytes));
+            RT_CUDA(ctx, cudaFuncSetAttribute(rhs_kernel<float, true, true, 1>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_bytes));
     }
     ctx->plan_valid = true;
     return RTBTE_OK;
@@ -706,6 +851,7 @@ static int launch_core_t(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStr
     P.groups = ctx->groups.as<Group>();
     P.n_groups = ctx->n_groups;
     P.mask = parts;
+    P.pf_dist = ctx->pf_dist;
     if (ctl && ctx->inst.size() > 1) {  // batched integration: balance over the active instances
         split_kernel<<<1, 256, 0, s>>>(ctx->groups.as<Group>(), ctx->n_groups, ctx->wpre.as<long long>(), ctl, parts,
                                        ctx->grid, ctx->n_items, ctx->dyn_tab.as<int>());
@@ -714,6 +860,9 @@ static int launch_core_t(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStr
         P.cta_items = ctx->dyn_tab.as<int>();
     } else {
         P.cta_items = ctx->cta_tab.as<int>() + (long long)(parts - 1) * (ctx->grid + 1);
+        P.tail = ctx->tail_tab.as<int4>() + ctx->tail_off[parts - 1];
+        P.n_tail = ctx->tail_off[parts] - ctx->tail_off[parts - 1];
+        P.tail_ctr = ctx->tail_ctr.as<int>();
     }
     P.partials = ctx->partials.p;
     P.popf = ctx->popf.p;
@@ -833,6 +982,50 @@ int autotune(rtbte_ctx *ctx, unsigned parts, int *chosen) {
                 rc = split_tables(ctx, best);
             }
         }
+    }
+    // L2 prefetch distance, then the share of the work split statically (the rest is taken
+    // dynamically by CTAs that finish early)
+    auto time3 = [&](float *ms) -> int {
+        int r2;
+        if ((r2 = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) return r2;
+        RT_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+        for (int r = 0; r < 3; ++r)
+            if ((r2 = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) return r2;
+        RT_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+        RT_CUDA(ctx, cudaEventSynchronize(e1));
+        RT_CUDA(ctx, cudaEventElapsedTime(ms, e0, e1));
+        return RTBTE_OK;
+    };
+    if (!rc) {
+        static const int dists[] = {0, 2, 3, 4, 6, 8};
+        int best_d = ctx->pf_dist;
+        float best_d_ms = 1e30f;
+        for (int d : dists) {
+            ctx->pf_dist = d;
+            float ms = 0.f;
+            if ((rc = time3(&ms))) break;
+            if (ms < best_d_ms) {
+                best_d_ms = ms;
+                best_d = d;
+            }
+        }
+        ctx->pf_dist = best_d;
+    }
+    if (!rc) {
+        static const double fracs[] = {1.0, 0.9, 0.8, 0.7, 0.6};
+        double best_f = 1.0;
+        float best_f_ms = 1e30f;
+        for (double f : fracs) {
+            ctx->static_frac = f;
+            float ms = 0.f;
+            if ((rc = split_tables(ctx, best)) || (rc = time3(&ms))) break;
+            if (ms < best_f_ms) {
+                best_f_ms = ms;
+                best_f = f;
+            }
+        }
+        ctx->static_frac = best_f;
+        if (!rc) rc = split_tables(ctx, best);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--accuracy-only", action="store_true", help="print only the error-versus-cost sweep")
+    ap.add_argument("--surrogate-only", action="store_true", help="print only the learned slow-stage study")
+    ap.add_argument("--direct-launches", action="store_true",
+                    help="integrator attempts by direct kernel launches instead of the device-loop graph "
+                         "(same kernels; for per-kernel launch lists)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: only standalone full-RHS evaluations (warm-up + steps), no JSON line")
     ap.add_argument("--grid", type=int, default=180, help="k/q grid side of the graphene-like workload (profiling)")
@@ -466,6 +470,8 @@ def run_ours(args):
     m = ri.graphene()
     ctx = rt.Context(m, precision="fp32", device=local_rank)
     ctx.upload_channels()
+    if args.direct_launches:
+        ctx.set_graph_mode(False)
     sz = ctx.sizes(0)
     stream = ctx.stream
     y = torch.tensor(m.y0(), device=dev)
@@ -599,7 +605,8 @@ def run_ours(args):
                                  "evaluation; populations are shared-memory staged by design" % (
                                      sz["channel_bytes"] / 1e9),
                            "channel_entries": entries, "replicas": world, "parallelism": f"replicas x{world}",
-                           "autotuned_split_weight": split_weight, "kernel_tuning": ctx.tuning()},
+                           "autotuned_split_weight": split_weight, "kernel_tuning": ctx.tuning(),
+                           "attempts": "direct launches" if args.direct_launches else "device-loop CUDA graph"},
                 "sim_ps_per_s": sim_ps * world / (tmax / 1000.0), "rhs_evals_timed": tot_rhs,
                 "sim_ps_per_s_at_rel_err_1e-6": (max(acc["sim_ps_per_s_at_1e-6"].values())
                                                  if acc and acc["sim_ps_per_s_at_1e-6"] else None),
@@ -625,6 +632,14 @@ def main():
         import rtbte_inputs as ri
 
         print(json.dumps(accuracy_sweep(rt, ri, torch.device("cuda", 0))), flush=True)
+        return 0
+    if args.surrogate_only:
+        import torch
+
+        import paper_2412_13402_gb300 as rt
+        import rtbte_inputs as ri
+
+        print(json.dumps(surrogate_study(rt, ri, torch.device("cuda", 0))), flush=True)
         return 0
     if args.impl == "reference":
         return run_reference(args)

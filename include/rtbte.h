@@ -245,6 +245,12 @@ int rtbte_autotune(rtbte_ctx *ctx, unsigned parts, int *chosen);
  * NULL).  Errors: INVALID_ARG. */
 int rtbte_get_tuning(const rtbte_ctx *ctx, int32_t *item_weight, int32_t *prefetch_items, double *static_share);
 
+/* How rtbte_advance_to runs attempts: 1 (default) as one launch of the device-loop CUDA graph
+ * per span; 0 as direct kernel launches, one attempt per host check (same kernels and results,
+ * slower; for per-kernel profiling tools that do not descend into graph loops).
+ * Errors: INVALID_ARG. */
+int rtbte_set_graph_mode(rtbte_ctx *ctx, int use_graphs);
+
 /* Kernel timing.  While enabled, every launch of the collision kernel enqueued outside a
  * CUDA graph (rtbte_rhs and the first-step estimate) is bracketed by CUDA events recorded on
  * the context stream.  rtbte_kernel_time synchronises the stream and returns the summed

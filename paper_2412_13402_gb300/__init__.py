@@ -34,7 +34,7 @@ HBAR_EV_PS = 6.582119569e-4
 
 EXPORTS = ["rtbte_desc_defaults", "rtbte_integ_defaults", "rtbte_create", "rtbte_upload_channels", "rtbte_rhs",
            "rtbte_advance_to", "rtbte_get_sizes", "rtbte_download_channels", "rtbte_set_stream",
-           "rtbte_autotune", "rtbte_get_tuning", "rtbte_set_kernel_timing", "rtbte_kernel_time", "rtbte_launch_count", "rtbte_last_error",
+           "rtbte_autotune", "rtbte_get_tuning", "rtbte_set_graph_mode", "rtbte_set_kernel_timing", "rtbte_kernel_time", "rtbte_launch_count", "rtbte_last_error",
            "rtbte_status_string", "rtbte_eph_rhs_noalloc", "rtbte_surrogate_create", "rtbte_surrogate_collect",
            "rtbte_surrogate_train", "rtbte_surrogate_predict", "rtbte_surrogate_loss_grad",
            "rtbte_surrogate_num_params", "rtbte_surrogate_get_params", "rtbte_surrogate_set_params",
@@ -120,6 +120,7 @@ def load():
         L.rtbte_set_stream.argtypes = [vp, vp]
         L.rtbte_autotune.argtypes = [vp, C.c_uint, vp]
         L.rtbte_get_tuning.argtypes = [vp, vp, vp, vp]
+        L.rtbte_set_graph_mode.argtypes = [vp, i32]
         L.rtbte_set_kernel_timing.argtypes = [vp, i32]
         L.rtbte_kernel_time.argtypes = [vp, vp, vp]
         L.rtbte_launch_count.argtypes = [vp]
@@ -331,6 +332,10 @@ class Context:
         w, d, sh = C.c_int32(), C.c_int32(), C.c_double()
         _check(self.ctx, load().rtbte_get_tuning(self.ctx, C.byref(w), C.byref(d), C.byref(sh)))
         return {"item_weight": w.value, "prefetch_items": d.value, "static_share": sh.value}
+
+    def set_graph_mode(self, use_graphs: bool):
+        """Attempts through the device-loop graph (default) or by direct launches."""
+        _check(self.ctx, load().rtbte_set_graph_mode(self.ctx, int(bool(use_graphs))))
 
     def set_kernel_timing(self, enable: bool):
         _check(self.ctx, load().rtbte_set_kernel_timing(self.ctx, int(bool(enable))))

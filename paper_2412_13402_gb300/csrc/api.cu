@@ -328,7 +328,7 @@ int rtbte_create(const rtbte_desc *d, rtbte_ctx **out) {
         (rc = dev_alloc(ctx, ctx->K, sizeof(double) * y * kMaxStages, true)) ||
         (rc = dev_alloc(ctx, ctx->Fs, sizeof(double) * y * 3, true)) ||
         (rc = dev_alloc(ctx, ctx->forcing, sizeof(double) * y, true)) ||
-        (rc = dev_alloc(ctx, ctx->wrms_part, sizeof(double) * 2 * y, true)) ||
+        (rc = dev_alloc(ctx, ctx->wrms_part, sizeof(double) * (2 * y + 2LL * kWrmsChunks * d->n_instances), true)) ||
         (rc = dev_alloc(ctx, ctx->ctl, sizeof(Ctl) * d->n_instances, true)))
         return bail(rc);
     if (cudaMallocHost(&ctx->ctl_host, sizeof(Ctl) * d->n_instances) != cudaSuccess)
@@ -443,6 +443,12 @@ int rtbte_get_tuning(const rtbte_ctx *ctx, int32_t *item_weight, int32_t *prefet
     if (item_weight) *item_weight = ctx->item_overhead;
     if (prefetch_items) *prefetch_items = ctx->pf_dist;
     if (static_share) *static_share = ctx->static_frac;
+    return RTBTE_OK;
+}
+
+int rtbte_set_graph_mode(rtbte_ctx *ctx, int use_graphs) {
+    if (!ctx) return RTBTE_E_INVALID_ARG;
+    ctx->use_graphs = use_graphs != 0;
     return RTBTE_OK;
 }
 

@@ -176,12 +176,27 @@ __device__ __forceinline__ void arm(Ctl *c) {
 }
 
 // One block per instance: WRMS norm (Eq. wrms_norm) of its rows, accept/reject, PID proposal.
-__global__ void controller_kernel(RowParams Q, Ctl *ctl, CtlParams cp, const double *wsq) {
+// Per-instance partial sums of a state-size vector: block (c, i) adds chunk c of instance i's
+// rows (fixed chunk boundaries and order, so the norms are deterministic); finished instances
+// are skipped when respect_done.
+__global__ void wrms_chunks(RowParams Q, const Ctl *ctl, const double *wsq, double *part, int respect_done) {
+    const int i = blockIdx.y;
+    if (respect_done && ctl[i].done) return;
+    const InstDev I = Q.inst[i];
+    const long long ni = (long long)I.n_c + I.n_ph;
+    const long long L = (ni + gridDim.x - 1) / gridDim.x;
+    const long long b = (long long)blockIdx.x * L;
+    const long long e = b + L < ni ? b + L : ni;
+    const double s = block_sum(wsq, I.y_off + b, e > b ? e - b : 0);
+    if (threadIdx.x == 0) part[(long long)i * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void controller_kernel(RowParams Q, Ctl *ctl, CtlParams cp, const double *part) {
     Ctl *c = ctl + blockIdx.x;
     if (c->done) return;
     const InstDev I = Q.inst[blockIdx.x];
     const long long ni = (long long)I.n_c + I.n_ph;
-    const double sum = block_sum(wsq, I.y_off, ni);
+    const double sum = block_sum(part, (long long)blockIdx.x * kWrmsChunks, kWrmsChunks);
     if (threadIdx.x != 0) return;
     const double eps = sqrt(sum / (double)ni);
     c->attempts++;
@@ -277,12 +292,12 @@ __global__ void __launch_bounds__(kRedThreads) h0_norms(RowParams Q, CtlParams c
     }
 }
 
-__global__ void h0_first(RowParams Q, Ctl *ctl, const double *wsq, long long n, double span) {
+__global__ void h0_first(RowParams Q, Ctl *ctl, const double *part0, const double *part1, double span) {
     Ctl *c = ctl + blockIdx.x;
     const InstDev I = Q.inst[blockIdx.x];
     const long long ni = (long long)I.n_c + I.n_ph;
-    const double s0 = block_sum(wsq, I.y_off, ni);
-    const double s1 = block_sum(wsq + n, I.y_off, ni);
+    const double s0 = block_sum(part0, (long long)blockIdx.x * kWrmsChunks, kWrmsChunks);
+    const double s1 = block_sum(part1, (long long)blockIdx.x * kWrmsChunks, kWrmsChunks);
     if (threadIdx.x != 0) return;
     const double d0 = sqrt(s0 / (double)ni), d1 = sqrt(s1 / (double)ni);
     double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
@@ -301,11 +316,11 @@ __global__ void h0_probe(RowParams Q, const Ctl *ctl, const double *Y0, const do
     }
 }
 
-__global__ void h0_second(RowParams Q, Ctl *ctl, CtlParams cp, const double *wsq, double span) {
+__global__ void h0_second(RowParams Q, Ctl *ctl, CtlParams cp, const double *part, double span) {
     Ctl *c = ctl + blockIdx.x;
     const InstDev I = Q.inst[blockIdx.x];
     const long long ni = (long long)I.n_c + I.n_ph;
-    const double s = block_sum(wsq, I.y_off, ni);
+    const double s = block_sum(part, (long long)blockIdx.x * kWrmsChunks, kWrmsChunks);
     if (threadIdx.x != 0) return;
     const double h0 = c->h0tmp, d1 = c->eps;
     const double d2 = sqrt(s / (double)ni) / h0;
@@ -401,10 +416,12 @@ int enqueue_attempt(rtbte_ctx *ctx, const Tableau &T, const CtlParams &cp, unsig
         a.stage = i;
         if ((rc = stage(ctx, a, s))) return rc;
     }
-    controller_kernel<<<n_inst(ctx), kRedThreads, 0, s>>>(row_params(ctx), ctx->ctl.as<Ctl>(), cp,
-                                                          ctx->wrms_part.as<double>());
+    double *chunks = ctx->wrms_part.as<double>() + 2 * ctx->n_y;
+    wrms_chunks<<<dim3(kWrmsChunks, n_inst(ctx)), kRedThreads, 0, s>>>(row_params(ctx), ctx->ctl.as<Ctl>(),
+                                                                      ctx->wrms_part.as<double>(), chunks, 1);
+    controller_kernel<<<n_inst(ctx), kRedThreads, 0, s>>>(row_params(ctx), ctx->ctl.as<Ctl>(), cp, chunks);
     RT_CUDA(ctx, cudaGetLastError());
-    ctx->launches++;
+    ctx->launches += 2;
     return RTBTE_OK;
 }
 
@@ -534,10 +551,21 @@ long long sum_attempts(rtbte_ctx *ctx) {
 // receives the instance-attempts performed (one per active instance per attempt).
 int run_attempts(rtbte_ctx *ctx, int method, const CtlParams &cp, unsigned parts, const double *forcing, int cap,
                  long long *attempts_out) {
-    cudaGraphExec_t ex;
-    int nl, rc;
-    if ((rc = attempt_graph(ctx, method, cp, parts, forcing, cap, &ex, &nl))) return rc;
     long long a0 = sum_attempts(ctx);
+    int rc;
+    if (!ctx->use_graphs) {  // direct launches, one attempt per host check (profilers, debugging)
+        const Tableau T = tableau_of(method);
+        for (;;) {
+            if ((rc = enqueue_attempt(ctx, T, cp, parts, forcing, ctx->stream))) return rc;
+            if ((rc = read_ctl(ctx))) return rc;
+            if (all_done(ctx)) break;
+        }
+        if (attempts_out) *attempts_out = sum_attempts(ctx) - a0;
+        return RTBTE_OK;
+    }
+    cudaGraphExec_t ex;
+    int nl;
+    if ((rc = attempt_graph(ctx, method, cp, parts, forcing, cap, &ex, &nl))) return rc;
     for (;;) {
         RT_CUDA(ctx, cudaGraphLaunch(ex, ctx->stream));
         RT_CUDA(ctx, cudaMemcpyAsync(ctx->loop_iter_host, ctx->loop_iter.p, sizeof(int), cudaMemcpyDeviceToHost,
@@ -563,9 +591,13 @@ int h0_estimate(rtbte_ctx *ctx, const CtlParams &cp, unsigned parts, const doubl
     if ((rc = stage(ctx, a, ctx->stream))) return rc;
     if ((rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) return rc;
     if ((rc = launch_rows(ctx, parts, K0, forcing, ctx->stream))) return rc;
+    double *part0 = wsq + 2 * ctx->n_y, *part1 = part0 + (long long)kWrmsChunks * n_inst(ctx);
+    const dim3 cg(kWrmsChunks, n_inst(ctx));
     h0_norms<<<nb, kRedThreads, 0, ctx->stream>>>(Q, cp, c, ctx->Y[0].as<double>(), ctx->Y[1].as<double>(), K0, K1,
                                                   wsq, 0, ctx->n_y);
-    h0_first<<<n_inst(ctx), kRedThreads, 0, ctx->stream>>>(Q, c, wsq, ctx->n_y, span);
+    wrms_chunks<<<cg, kRedThreads, 0, ctx->stream>>>(Q, c, wsq, part0, 0);
+    wrms_chunks<<<cg, kRedThreads, 0, ctx->stream>>>(Q, c, wsq + ctx->n_y, part1, 0);
+    h0_first<<<n_inst(ctx), kRedThreads, 0, ctx->stream>>>(Q, c, part0, part1, span);
     if (ctx->precision == RTBTE_PREC_FP64)
         h0_probe<double><<<nb, kRedThreads, 0, ctx->stream>>>(Q, c, ctx->Y[0].as<double>(), ctx->Y[1].as<double>(), K0,
                                                               ctx->n_y);
@@ -573,14 +605,15 @@ int h0_estimate(rtbte_ctx *ctx, const CtlParams &cp, unsigned parts, const doubl
         h0_probe<float><<<nb, kRedThreads, 0, ctx->stream>>>(Q, c, ctx->Y[0].as<double>(), ctx->Y[1].as<double>(), K0,
                                                              ctx->n_y);
     RT_CUDA(ctx, cudaGetLastError());
-    ctx->launches += 3;
+    ctx->launches += 5;
     if ((rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) return rc;
     if ((rc = launch_rows(ctx, parts, K1, forcing, ctx->stream))) return rc;
     h0_norms<<<nb, kRedThreads, 0, ctx->stream>>>(Q, cp, c, ctx->Y[0].as<double>(), ctx->Y[1].as<double>(), K0, K1,
                                                   wsq, 1, ctx->n_y);
-    h0_second<<<n_inst(ctx), kRedThreads, 0, ctx->stream>>>(Q, c, cp, wsq, span);
+    wrms_chunks<<<cg, kRedThreads, 0, ctx->stream>>>(Q, c, wsq, part0, 0);
+    h0_second<<<n_inst(ctx), kRedThreads, 0, ctx->stream>>>(Q, c, cp, part0, span);
     RT_CUDA(ctx, cudaGetLastError());
-    ctx->launches += 2;
+    ctx->launches += 3;
     return RTBTE_OK;
 }
 

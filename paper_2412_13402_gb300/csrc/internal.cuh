@@ -34,6 +34,7 @@ constexpr int kRhsThreads = 512;
 constexpr int kMaxModes = 16;
 constexpr int kMaxStages = 5;
 constexpr int kWrmsBlocks = 512;
+constexpr int kWrmsChunks = 128;  // per-instance blocks of the WRMS reduction before the controller
 constexpr int kLoopCap = 64;     // attempts per launch of an attempt-loop graph (default)
 
 enum { PART_EPH = 0, PART_PHE = 1, PART_PP = 2 };
@@ -206,10 +207,11 @@ struct rtbte_ctx {
     int num_sms = 0;
     size_t smem_optin = 0;
     // integrator work buffers
-    rtbte::DevBuf Y[2], K, Fs, forcing, wrms_part, ctl, ystage, ydstage;  // wrms_part: 2 x n_y squared norms
+    rtbte::DevBuf Y[2], K, Fs, forcing, wrms_part, ctl, ystage, ydstage;  // wrms_part: 2 x n_y squared norms, then per-instance chunk sums
     rtbte::Ctl *ctl_host = nullptr;  // pinned mirror of the per-instance controllers
     std::map<long long, cudaGraphExec_t> graphs;
     std::map<long long, int> graph_launches;  // kernels per attempt of each attempt-loop graph
+    bool use_graphs = true;                   // attempts through the device-loop graph (else direct launches)
     rtbte::DevBuf loop_iter;                  // attempts run by the last attempt-loop launch (device)
     int *loop_iter_host = nullptr;            // pinned mirror
     long long launches = 0;

@@ -389,3 +389,25 @@ def test_status_codes(rt):
     st = ctx.advance_to(0.01, bad, method="zon43", t0=0.0)
     assert st["rc"] == -7
     ctx.close()
+
+
+@pytest.mark.parametrize("method", ["zon43", "mri"])
+def test_device_loop_graph_equals_direct_launches(rt, method):
+    """The device-side attempt loop (a CUDA graph with a WHILE node) runs the same kernels as
+    direct launches with a host check after every attempt: identical states and counts."""
+    m = ri.graphene_small(36)
+    kw = dict(rtol=1e-5, atol_c=1e-9, atol_ph=1e-12)
+    if method == "mri":
+        kw["h_s"] = 0.01
+    out = []
+    for graphs in (True, False):
+        ctx = rt.Context(m)
+        ctx.upload_channels()
+        ctx.set_graph_mode(graphs)
+        y = torch.tensor(m.y0(), device="cuda")
+        st = ctx.advance_to(0.03, y, method=method, t0=0.0, **kw)
+        assert st["status"] == 0
+        out.append((y.cpu().numpy(), st["steps"], st["attempts"]))
+        ctx.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1:] == out[1][1:]

@@ -310,10 +310,17 @@ class Context:
         rtbte_rhs(self.ctx, t, y.data_ptr(), ydot.data_ptr(), parts)
         return ydot
 
-    def advance_to(self, t_out: float, y, **opts) -> dict:
+    def advance_to(self, t_out: float, y, options: "Integ | None" = None, stats: "Stats | None" = None, **opts):
+        """Integrate the device state y to t_out.  With keyword options: returns a dict of the
+        statistics.  With a prebuilt `options` (integ_options(...)) and a reusable `stats`
+        object: fills and returns `stats` (no per-call allocation, for tight driver loops)."""
         import torch
 
         assert y.is_cuda and y.dtype == torch.float64 and y.is_contiguous()
+        if options is not None:
+            st = stats if stats is not None else Stats()
+            rtbte_advance_to(self.ctx, t_out, y.data_ptr(), options, st)
+            return st
         o = integ_options(**opts)
         st = Stats()
         rc = rtbte_advance_to(self.ctx, t_out, y.data_ptr(), o, st)

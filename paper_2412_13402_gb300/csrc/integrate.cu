@@ -119,9 +119,11 @@ __global__ void __launch_bounds__(kRedThreads) stage_kernel(RowParams Q, StageAr
         if (a.forcing) k += a.forcing[c];
         a.K[(long long)i * a.n + c] = k;
         if (i < S - 1) {
-            double acc = 0.0;
-            for (int j = 0; j <= i; ++j) acc += a.T.A[i + 1][j] * a.K[(long long)j * a.n + c];
-            write_pops<R>(Q, I, local, y[c] + h * acc);
+            // the next stage state only feeds the population copies in precision R: in FP32 the
+            // stage combination is formed in FP32 (its rounding is below the copy's)
+            R acc = R(0);
+            for (int j = 0; j <= i; ++j) acc += (R)a.T.A[i + 1][j] * (R)a.K[(long long)j * a.n + c];
+            write_pops<R>(Q, I, local, (R)y[c] + (R)h * acc);
         } else {
             double s1 = 0.0, s2 = 0.0;
             for (int j = 0; j < S; ++j) {
@@ -132,10 +134,10 @@ __global__ void __launch_bounds__(kRedThreads) stage_kernel(RowParams Q, StageAr
             const double ynew = y[c] + h * s1;
             (C->cur ? a.Y0 : a.Y1)[c] = ynew;
             double x2 = 0.0;
-            if (a.T.has_emb) {
+            if (a.T.has_emb) {  // error weight in precision R (a relative 1e-7 in the norm is immaterial)
                 const double e = h * s2;
-                const double w = 1.0 / (a.cp.rtol * fabs(y[c]) + atol_of(a.cp, I, local));
-                const double x = e * w;
+                const R w = R(1) / ((R)a.cp.rtol * (R)fabs(y[c]) + (R)atol_of(a.cp, I, local));
+                const double x = (double)((R)e * w);
                 x2 = x * x;
             }
             if (!isfinite(ynew)) x2 = __longlong_as_double(0x7ff8000000000000LL);
@@ -527,10 +529,11 @@ int read_ctl(rtbte_ctx *ctx) {
     return RTBTE_OK;
 }
 
+// Stream-ordered copy of the pinned host mirror to the device; the host does not write the
+// mirror again before the next read_ctl (which synchronises), so no wait is needed here.
 int write_ctl(rtbte_ctx *ctx) {
     RT_CUDA(ctx, cudaMemcpyAsync(ctx->ctl.p, ctx->ctl_host, sizeof(Ctl) * n_inst(ctx), cudaMemcpyHostToDevice,
                                  ctx->stream));
-    RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return RTBTE_OK;
 }
 

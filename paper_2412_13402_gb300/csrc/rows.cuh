@@ -28,57 +28,74 @@ __device__ __forceinline__ int find_inst(const RowParams &Q, long long comp) {
     return lo;
 }
 
-template <class R>
-__device__ __forceinline__ double item_sum(const RowParams &Q, int i0, int i1) {
-    const R *P = reinterpret_cast<const R *>(Q.partials);
+// Accumulator of item partials (hi, lo) in item order.  FP64 partials add in FP64.  FP32
+// partials add as an FP32 head/tail pair (two-sum on the heads, tails summed) and are widened
+// once at the end: about 48 significant bits, far below the partials' own rounding, with no
+// FP64 arithmetic per item (FP64 throughput is low on this GPU).
+template <class R> struct RowAcc {
     double acc = 0.0;
-    for (int it = i0; it < i1; ++it) acc += (double)P[2 * it] + (double)P[2 * it + 1];
-    return acc;
+    __device__ __forceinline__ void add(R hi, R lo) { acc += (double)hi + (double)lo; }
+    __device__ __forceinline__ double value() const { return acc; }
+};
+template <> struct RowAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float hi, float lo) {
+        const float t = s + hi;
+        const float bp = t - s;
+        c += ((s - (t - bp)) + (hi - bp)) + lo;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <class R>
+__device__ __forceinline__ void item_sum(const RowParams &Q, int i0, int i1, RowAcc<R> &A) {
+    const R *P = reinterpret_cast<const R *>(Q.partials);
+    for (int it = i0; it < i1; ++it) A.add(P[2 * it], P[2 * it + 1]);
 }
 
 // RHS value of row `local` of instance I for the selected parts.
 template <class R>
 __device__ __forceinline__ double row_value(const RowParams &Q, const InstDev &I, long long local, unsigned parts) {
+    RowAcc<R> A;
     if (local < I.n_c) {
         if (!(parts & RTBTE_EPH)) return 0.0;
         const int d = (int)local;
-        double acc = 0.0;
         for (int nu = 0; nu < I.nmodes; ++nu) {
             const int *o = Q.eoff + I.eoff_base + (long long)nu * (I.n_c + 1);
-            acc += item_sum<R>(Q, o[d], o[d + 1]);
+            item_sum<R>(Q, o[d], o[d + 1], A);
         }
-        return -acc;
+        return -A.value();
     }
     const long long p = local - I.n_c;
-    double acc = 0.0;
     if (parts & RTBTE_PHE) {
         const int *o = Q.poff + I.poff_base;
-        acc += item_sum<R>(Q, o[p], o[p + 1]);
+        item_sum<R>(Q, o[p], o[p + 1], A);
     }
     if ((parts & RTBTE_PHPH) && I.M > 0) {
         const int a = Q.compact[I.compact_base + p];
         if (a >= 0) {
             const int *o = Q.ppoff + I.ppoff_base;
-            acc += item_sum<R>(Q, o[a], o[a + 1]);
+            item_sum<R>(Q, o[a], o[a + 1], A);
         }
     }
-    return -acc;
+    return -A.value();
 }
 
 // Store component value v of row `local` into the population copies read by the RHS.
 template <class R>
-__device__ __forceinline__ void write_pops(const RowParams &Q, const InstDev &I, long long local, double v) {
+__device__ __forceinline__ void write_pops(const RowParams &Q, const InstDev &I, long long local, R v) {
     if (local < I.n_c) {
-        reinterpret_cast<R *>(Q.popf)[I.f_off + local] = (R)v;
+        reinterpret_cast<R *>(Q.popf)[I.f_off + local] = v;
         return;
     }
     const long long p = local - I.n_c;
     const int nu = (int)(p / I.N_q);
     const long long q = p - (long long)nu * I.N_q;
-    reinterpret_cast<R *>(Q.popN)[I.N_off + (long long)nu * I.N_q_pad + q] = (R)v;
+    reinterpret_cast<R *>(Q.popN)[I.N_off + (long long)nu * I.N_q_pad + q] = v;
     if (I.M > 0) {
         const int a = Q.compact[I.compact_base + p];
-        if (a >= 0) reinterpret_cast<R *>(Q.popP)[I.P_off + a] = (R)v;
+        if (a >= 0) reinterpret_cast<R *>(Q.popP)[I.P_off + a] = v;
     }
 }
 

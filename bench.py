@@ -519,14 +519,9 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     launches = ctx.launch_count() - launches0
     sim_ps = args.steps * WINDOW_PS
-    tot_rhs, tmax = n_rhs, ms
-    if dist is not None:
-        v = torch.tensor([float(n_rhs)], device=dev)
-        dist.all_reduce(v)
-        tot_rhs = v.item()
-        v = torch.tensor([ms], device=dev)
-        dist.all_reduce(v, op=dist.ReduceOp.MAX)
-        tmax = v.item()
+    from paper_2412_13402_gb300 import ranks
+
+    tot_rhs, tmax = ranks.job_throughput(n_rhs, ms, dist, dev)  # units over all ranks / slowest rank
     value = tot_rhs / (tmax / 1000.0)
 
     # ---- roofline: collision kernel alone, CUDA events on the library stream

@@ -119,11 +119,9 @@ __global__ void __launch_bounds__(kRedThreads) stage_kernel(RowParams Q, StageAr
         if (a.forcing) k += a.forcing[c];
         a.K[(long long)i * a.n + c] = k;
         if (i < S - 1) {
-            // the next stage state only feeds the population copies in precision R: in FP32 the
-            // stage combination is formed in FP32 (its rounding is below the copy's)
-            R acc = R(0);
-            for (int j = 0; j <= i; ++j) acc += (R)a.T.A[i + 1][j] * (R)a.K[(long long)j * a.n + c];
-            write_pops<R>(Q, I, local, (R)y[c] + (R)h * acc);
+            double acc = 0.0;
+            for (int j = 0; j <= i; ++j) acc += a.T.A[i + 1][j] * a.K[(long long)j * a.n + c];
+            write_pops<R>(Q, I, local, (R)(y[c] + h * acc));
         } else {
             double s1 = 0.0, s2 = 0.0;
             for (int j = 0; j < S; ++j) {

@@ -786,10 +786,29 @@ int make_plan(rtbte_ctx *ctx) {
         D.compact_base = (long long)compact.size();
         compact.insert(compact.end(), I.compact.begin(), I.compact.end());
     }
-    // staging decision and launch shape
+    // staging decision and launch shape: 16 warps per SM, as 1, 2 or 4 CTAs -- several CTAs
+    // per SM when their staging fits, so one CTA's group change (barrier + staging copy)
+    // overlaps the others' streaming
     ctx->staged = max_stage + 64 <= ctx->smem_optin;  // 64 B left for the kernel's static shared memory
     ctx->smem_bytes = ctx->staged ? std::max<size_t>(max_stage, 16) : 0;
-    ctx->grid = ctx->num_sms * (ctx->staged ? 1 : 2);
+    int per_sm = 1;
+    ctx->threads = kRhsThreads;
+    if (ctx->staged) {
+        const void *kfn = ctx->precision == RTBTE_PREC_FP64 ? (const void *)rhs_kernel<double, true, false, 1>
+                                                             : (const void *)rhs_kernel<float, true, true, 1>;
+        RT_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_bytes));
+        RT_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        for (int k : {4, 2}) {
+            int nb = 0;
+            RT_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, kRhsThreads / k, ctx->smem_bytes));
+            if (nb >= k) {
+                per_sm = k;
+                break;
+            }
+        }
+        ctx->threads = kRhsThreads / per_sm;
+    }
+    ctx->grid = ctx->num_sms * (ctx->staged ? per_sm : 2);
     ctx->item_len_h.resize(items.size());
     for (size_t k = 0; k < items.size(); ++k) ctx->item_len_h[k] = items[k].len;
     ctx->group_begin_h.resize(groups.size());
@@ -818,14 +837,6 @@ int make_plan(rtbte_ctx *ctx) {
     ctx->partials.bytes = pb;
     RT_CUDA(ctx, cudaMemsetAsync(ctx->partials.p, 0, pb, ctx->stream));
     RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (ctx->staged) {
-        if (ctx->precision == RTBTE_PREC_FP64)
-            RT_CUDA(ctx, cudaFuncSetAttribute(rhs_kernel<double, true, false, 1>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_bytes));
-        else
-            RT_CUDA(ctx, cudaFuncSetAttribute(rhs_kernel<float, true, true, 1>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_bytes));
-    }
     ctx->plan_valid = true;
     return RTBTE_OK;
 }

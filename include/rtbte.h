@@ -207,6 +207,16 @@ int rtbte_upload_channels(rtbte_ctx *ctx, int inst, const rtbte_channels *ch);
  * Errors: STATE (some instance has no channels), INVALID_ARG, CUDA. */
 int rtbte_rhs(rtbte_ctx *ctx, double t, const double *y, double *ydot, unsigned parts);
 
+/* Linearised ph-ph scattering rates (the mode-resolved phonon rates used to converge grids,
+ * Methods: computational details; Eq. ph-ph differentiated in the destination population):
+ *   rates[row(a)] = -dI^{ph-ph}_a/dN_a = sum_em W (N' + N'' + 1) + sum_abs W (N'' - N')
+ * over the stored ph-ph channels of each sub-lattice phonon a (W as stored: pair and
+ * absorption factors included), at the DEVICE state y (FP64 [n_y]); every other row of the
+ * DEVICE output rates (FP64 [n_y]) is 0.  Populations in the compute precision, sums in FP64.
+ * At Bose-Einstein populations this is the inverse relaxation time of each phonon.  Enqueued
+ * on the context's stream.  Errors: INVALID_ARG, STATE (no channels), CUDA. */
+int rtbte_phph_rates(rtbte_ctx *ctx, const double *y, double *rates);
+
 /* Advance the device state y (FP64 [n_y_total], caller-owned) from opt->t0 to t_out with
  * the method of `opt`.  All stepping, error norms and step-size control run on the device:
  * each integration span is one launch of a CUDA graph whose WHILE node repeats the attempt

@@ -207,6 +207,24 @@ class Oracle:
         L.or_pp_fill(self.ptr, n, _p(d), _p(off), _p(b), _p(c), _p(W))
         return dict(off=off, b=b, c=c, W=W, full=full)
 
+    def pp_rates(self, y):
+        """Linearised ph-ph rates (Eq. ph-ph differentiated in the destination population):
+        for every sub-lattice phonon a, -dI_a/dN_a = sum_em W (N_b + N_c + 1) + sum_abs W (N_c - N_b)
+        over its stored channels (W with the pair and absorption factors).  Returns a
+        state-size vector, 0 outside the sub-lattice rows."""
+        y = np.ascontiguousarray(y, np.float64)
+        m = self.model
+        L = self.lists["pp"] if self.lists is not None and self.lists.get("pp") is not None else self.pp_lists()
+        N = y[m.n_c:][L["full"]]  # populations of the sub-lattice, compact order
+        out = np.zeros_like(y)
+        off, b, c, W = L["off"], L["b"], L["c"], L["W"]
+        for a in range(L["full"].shape[0]):
+            e0, e1, e2 = off[2 * a], off[2 * a + 1], off[2 * a + 2]
+            em = np.sum(W[e0:e1] * (N[b[e0:e1]] + N[c[e0:e1]] + 1.0))
+            ab = np.sum(W[e1:e2] * (N[c[e1:e2]] - N[b[e1:e2]]))
+            out[m.n_c + L["full"][a]] = em + ab
+        return out
+
     def build_lists(self, parts=ALL):
         self.lists = dict(eph=self.eph_lists() if parts & (EPH | PHE) else None,
                           phe=self.phe_lists() if parts & PHE else None,

@@ -33,7 +33,7 @@ RTBTE_RK4, RTBTE_BS32, RTBTE_ZON43, RTBTE_MRI_KW3, RTBTE_SPLIT_RK4 = 0, 1, 2, 3,
 HBAR_EV_PS = 6.582119569e-4
 
 EXPORTS = ["rtbte_desc_defaults", "rtbte_integ_defaults", "rtbte_create", "rtbte_upload_channels", "rtbte_rhs",
-           "rtbte_advance_to", "rtbte_get_sizes", "rtbte_download_channels", "rtbte_set_stream",
+           "rtbte_advance_to", "rtbte_phph_rates", "rtbte_get_sizes", "rtbte_download_channels", "rtbte_set_stream",
            "rtbte_autotune", "rtbte_get_tuning", "rtbte_set_graph_mode", "rtbte_set_kernel_timing", "rtbte_kernel_time", "rtbte_launch_count", "rtbte_last_error",
            "rtbte_status_string", "rtbte_eph_rhs_noalloc", "rtbte_surrogate_create", "rtbte_surrogate_collect",
            "rtbte_surrogate_train", "rtbte_surrogate_predict", "rtbte_surrogate_loss_grad",
@@ -115,6 +115,7 @@ def load():
         L.rtbte_upload_channels.argtypes = [vp, i32, vp]
         L.rtbte_rhs.argtypes = [vp, dbl, vp, vp, C.c_uint]
         L.rtbte_advance_to.argtypes = [vp, dbl, vp, vp, vp]
+        L.rtbte_phph_rates.argtypes = [vp, vp, vp]
         L.rtbte_get_sizes.argtypes = [vp, i32, vp]
         L.rtbte_download_channels.argtypes = [vp, i32, C.c_uint, vp, vp, vp, vp]
         L.rtbte_set_stream.argtypes = [vp, vp]
@@ -327,6 +328,15 @@ class Context:
         d = st.as_dict()
         d["rc"] = rc
         return d
+
+    def phph_rates(self, y):
+        """Linearised ph-ph rates -dI^{ph-ph}_a/dN_a on the sub-lattice rows (0 elsewhere)."""
+        import torch
+
+        assert y.is_cuda and y.dtype == torch.float64 and y.is_contiguous()
+        out = torch.empty_like(y)
+        _check(self.ctx, load().rtbte_phph_rates(self.ctx, y.data_ptr(), out.data_ptr()))
+        return out
 
     def autotune(self, parts: int = RTBTE_ALL) -> int:
         """Pick the collision kernel's work-split weight by timing; returns the chosen weight."""

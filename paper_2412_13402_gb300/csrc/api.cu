@@ -173,6 +173,7 @@ int upload_prebuilt(rtbte_ctx *ctx, InstHost &I, const rtbte_channels *ch) {
     if (rc) return rc;
     I.pp_cnt.clear();
     I.pp_off.assign(1, 0);
+    I.pp_off_dev.release();
     I.pp_idx.release();
     I.pp_W.release();
     if (I.M > 0) {
@@ -378,6 +379,19 @@ int rtbte_rhs(rtbte_ctx *ctx, double t, const double *y, double *ydot, unsigned 
     return RTBTE_OK;
 }
 
+int rtbte_phph_rates(rtbte_ctx *ctx, const double *y, double *rates) {
+    if (!ctx) return RTBTE_E_INVALID_ARG;
+    if (!y || !rates || !ptr_is_device(y) || !ptr_is_device(rates))
+        return fail(ctx, RTBTE_E_INVALID_ARG, "y and rates must be device pointers");
+    int rc;
+    if ((rc = ensure_plan(ctx))) return rc;
+    RT_CUDA(ctx, cudaMemsetAsync(rates, 0, sizeof(double) * ctx->n_y, ctx->stream));
+    if ((rc = launch_prep_from_y(ctx, y, ctx->stream))) return rc;
+    for (int i = 0; i < (int)ctx->inst.size(); ++i)
+        if ((rc = launch_pp_rates(ctx, i, rates, ctx->stream))) return rc;
+    return RTBTE_OK;
+}
+
 int rtbte_advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *opt, rtbte_stats *st) {
     if (!ctx) return RTBTE_E_INVALID_ARG;
     if (!y || !opt) return fail(ctx, RTBTE_E_INVALID_ARG, "bad advance_to arguments");
@@ -506,7 +520,8 @@ void rtbte_destroy(rtbte_ctx *ctx) {
     ctx->loop_iter_host = nullptr;
     for (auto &I : ctx->inst) {
         DevBuf *bufs[] = {&I.t_ek, &I.t_eps, &I.t_eid, &I.t_eidinv, &I.t_omega, &I.t_kmap, &I.t_lut, &I.t_g2,
-                          &I.t_ppfull, &I.t_ppinv, &I.eph_idx, &I.eph_W, &I.phe_idx, &I.phe_W, &I.pp_idx, &I.pp_W};
+                          &I.t_ppfull, &I.t_ppinv, &I.eph_idx, &I.eph_W, &I.phe_idx, &I.phe_W, &I.pp_idx, &I.pp_W,
+                          &I.pp_off_dev};
         for (DevBuf *b : bufs) b->release();
     }
     ctx->tail_tab.release();

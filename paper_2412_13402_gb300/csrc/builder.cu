@@ -442,6 +442,7 @@ int run_build(rtbte_ctx *ctx, InstHost &I) {
     // ---- ph-ph
     I.pp_cnt.clear();
     I.pp_off.assign(1, 0);
+    I.pp_off_dev.release();
     I.pp_idx.release();
     I.pp_W.release();
     if (I.M > 0) {

@@ -169,6 +169,7 @@ struct InstHost {
     // channel lists (device)
     DevBuf eph_idx, eph_W, phe_idx, phe_W, pp_idx, pp_W;
     std::vector<long long> eph_off, phe_off, pp_off;  // padded CSR offsets (host copy)
+    DevBuf pp_off_dev;                                // device copy of pp_off (made on first use)
     std::vector<long long> eph_cnt, phe_cnt, pp_cnt;  // logical counts per segment
     bool has_channels = false;
     long long y_off = 0, f_off = 0, N_off = 0, P_off = 0;
@@ -243,6 +244,7 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *opt, 
 void destroy_graphs(rtbte_ctx *ctx);
 // api.cu
 int fail(rtbte_ctx *ctx, int code, const std::string &msg);
+int launch_pp_rates(rtbte_ctx *ctx, int inst, double *rates, cudaStream_t s);
 // Surrogate slow value (control variate about the last exact reference) at the device state y,
 // written to dst [n_y]; and the judge, which compares that value with the exact one and makes
 // (y, exact) the new reference (*relerr < 0 when there was no reference yet).

@@ -1045,6 +1045,54 @@ int autotune(rtbte_ctx *ctx, unsigned parts, int *chosen) {
     return RTBTE_OK;
 }
 
+// Linearised ph-ph rates: one warp per sub-lattice destination a of one instance,
+//   Gamma_a = -dI^{ph-ph}_a/dN_a = sum_em W (N' + N'' + 1) + sum_abs W (N'' - N')
+// (Eq. ph-ph with G_em, G_abs differentiated in the destination population; W as stored,
+// pair and absorption factors included), from the compute-precision sub-lattice copy popP,
+// summed in FP64 per lane then a fixed butterfly; written to rates[y_off + n_c + full(a)].
+template <class R>
+__global__ void pp_rates_kernel(const uint32_t *idx, const R *W, const long long *off, const R *P, const int *pp_full,
+                                int pp_bits, long long M, long long row0, double *rates) {
+    const int lane = threadIdx.x & 31;
+    const unsigned pmask = (1u << pp_bits) - 1u;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long a = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; a < M; a += nw) {
+        double acc = 0.0;
+        for (int proc = 0; proc < 2; ++proc)
+            for (long long e = off[2 * a + proc] + lane; e < off[2 * a + proc + 1]; e += 32) {
+                const uint32_t x = idx[e];
+                const double Nb = (double)P[x & pmask], Nc = (double)P[x >> pp_bits];
+                acc += (double)W[e] * (proc == 0 ? Nb + Nc + 1.0 : Nc - Nb);
+            }
+#pragma unroll
+        for (int m = 16; m; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+        if (lane == 0) rates[row0 + pp_full[a]] = acc;
+    }
+}
+
+int launch_pp_rates(rtbte_ctx *ctx, int inst, double *rates, cudaStream_t s) {
+    InstHost &I = ctx->inst[inst];
+    if (I.M == 0) return RTBTE_OK;
+    if (!I.pp_off_dev.p) {
+        RT_CUDA(ctx, cudaMalloc(&I.pp_off_dev.p, sizeof(long long) * I.pp_off.size()));
+        I.pp_off_dev.bytes = sizeof(long long) * I.pp_off.size();
+        RT_CUDA(ctx, cudaMemcpyAsync(I.pp_off_dev.p, I.pp_off.data(), I.pp_off_dev.bytes, cudaMemcpyHostToDevice, s));
+    }
+    const int blocks = (int)std::min<long long>((I.M + 7) / 8, 8LL * ctx->num_sms);
+    if (ctx->precision == RTBTE_PREC_FP64)
+        pp_rates_kernel<double><<<blocks, 256, 0, s>>>(I.pp_idx.as<uint32_t>(), I.pp_W.as<double>(),
+                                                       I.pp_off_dev.as<long long>(),
+                                                       ctx->popP.as<double>() + I.P_off, I.t_ppfull.as<int>(),
+                                                       I.pp_bits, I.M, I.y_off + I.d.n_c, rates);
+    else
+        pp_rates_kernel<float><<<blocks, 256, 0, s>>>(I.pp_idx.as<uint32_t>(), I.pp_W.as<float>(),
+                                                      I.pp_off_dev.as<long long>(), ctx->popP.as<float>() + I.P_off,
+                                                      I.t_ppfull.as<int>(), I.pp_bits, I.M, I.y_off + I.d.n_c, rates);
+    RT_CUDA(ctx, cudaGetLastError());
+    ctx->launches++;
+    return RTBTE_OK;
+}
+
 int launch_rows(rtbte_ctx *ctx, unsigned parts, double *out, const double *forcing, cudaStream_t s) {
     RowParams Q = row_params(ctx);
     const int threads = 256;

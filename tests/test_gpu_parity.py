@@ -411,3 +411,21 @@ def test_device_loop_graph_equals_direct_launches(rt, method):
         ctx.close()
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1:] == out[1][1:]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp64", 1e-12)])
+def test_linearised_phph_rates_match_oracle(rt, oracle_lib, prec, tol):
+    """rtbte_phph_rates against the oracle's sums over the same channel lists, at random
+    populations and at the Bose-Einstein start; zero outside the ph-ph sub-lattice."""
+    m = ri.graphene_small(36)
+    o = oracle_lib.Oracle(m)
+    o.build_lists()
+    ctx = rt.Context(m, precision=prec)
+    ctx.upload_channels()
+    f, N = ri.random_populations(m, 9)
+    for y_np in (np.concatenate([f, N]), m.y0()):
+        got = ctx.phph_rates(torch.tensor(y_np, device="cuda")).cpu().numpy()
+        ref = o.pp_rates(y_np)
+        assert relL2(got, ref) < tol
+        assert not got[ref == 0].any()
+    ctx.close()

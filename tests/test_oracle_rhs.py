@@ -272,3 +272,40 @@ def test_frozen_modes_do_not_scatter(oracle_lib):
     assert (cnt[fr] == 0).all()
     r = o.rhs(symmetric_state(m, 1))
     assert (r[m.n_c:][fr] == 0).all()
+
+
+def test_linearised_phph_rates_are_the_derivative_of_the_integral(oracle_lib):
+    """The linearised ph-ph rate of a sub-lattice phonon (partners held fixed) equals minus
+    the derivative of its literal Eq. ph-ph integral with respect to its own population,
+    checked by central differences of the plain sums on phonons that are not their own
+    partner in any channel (there the integral is affine in the population; a phonon can
+    absorb one of its own kind, a + a -> b, which makes the full derivative differ)."""
+    m = ri.graphene_small(24)
+    o = oracle_lib.Oracle(m)
+    L = o.build_lists()["pp"]
+    f, N = ri.random_populations(m, 8)
+    y = np.concatenate([f, N])
+    rates = o.pp_rates(y)
+    full = o.pp_full_index()
+    off = L["off"]
+    own = [a for a in range(full.shape[0])
+           if not np.any(L["b"][off[2 * a]:off[2 * a + 2]] == a) and not np.any(L["c"][off[2 * a]:off[2 * a + 2]] == a)]
+    assert len(own) > full.shape[0] // 4
+    rng = np.random.default_rng(2)
+    for a in rng.choice(own, 8, replace=False):
+        r = m.n_c + full[a]
+        pmask = np.zeros(m.n_ph, np.uint8)
+        pmask[full[a]] = 1
+        d = 1e-3 * max(1.0, y[r])
+        yp, ym = y.copy(), y.copy()
+        yp[r] += d
+        ym[r] -= d
+        ip = o.rhs_literal(yp, parts=oracle_lib.PHPH, pmask=pmask)[r]
+        im = o.rhs_literal(ym, parts=oracle_lib.PHPH, pmask=pmask)[r]
+        assert -(ip - im) / (2 * d) == pytest.approx(rates[r], rel=1e-9, abs=1e-12 * abs(rates).max())
+    mask = np.ones(m.n_y, bool)
+    mask[m.n_c + full] = False
+    assert not rates[mask].any()
+    # at Bose-Einstein populations (one temperature) the optical branches relax (positive rates)
+    rb = o.pp_rates(m.y0())[m.n_c + full].reshape(m.nmodes, -1)
+    assert (rb[3:] > 0).all()

@@ -166,7 +166,21 @@ typedef struct rtbte_integ {
     double safety, growth, growth_first, etamxf, etamin; /* 0: library defaults          */
     int32_t small_nef;     /* failures before etamxf applies (default 2)                  */
     int32_t chunk;         /* attempts per launch of the device attempt loop (0: 64)      */
+    int32_t resume;        /* 1: continue the controller of the previous call (step proposal,
+                              error history; no first-step estimate) -- see rtbte_controller */
+    int32_t reserved2;
 } rtbte_integ;
+
+/* Step-size controller state of one instance (Eq. pid_controller), for checkpointing: save it
+ * with the state vector after rtbte_advance_to, restore both into a new context, and a call
+ * with opt->resume = 1 continues exactly as the uninterrupted run would. */
+typedef struct rtbte_controller {
+    double t;          /* time of the state it belongs to                                   */
+    double h;          /* next step proposal                                                */
+    double eps1, eps2; /* error history eps_{k-1}, eps_{k-2}                                */
+    int32_t first;     /* 1 before the first accepted step                                  */
+    int32_t nef;       /* consecutive error-test failures                                   */
+} rtbte_controller;
 
 typedef struct rtbte_stats {
     int64_t steps, attempts, fails;      /* accepted steps, attempts, error-test fails    */
@@ -206,6 +220,12 @@ int rtbte_upload_channels(rtbte_ctx *ctx, int inst, const rtbte_channels *ch);
  * context, synchronous).  Rows of parts not selected are written as 0.
  * Errors: STATE (some instance has no channels), INVALID_ARG, CUDA. */
 int rtbte_rhs(rtbte_ctx *ctx, double t, const double *y, double *ydot, unsigned parts);
+
+/* Read / write the controller state of instance `inst` (host memory).  get reflects the end
+ * of the last rtbte_advance_to (or the last set); set takes effect at the next call with
+ * opt->resume = 1.  Errors: INVALID_ARG. */
+int rtbte_get_controller(const rtbte_ctx *ctx, int inst, rtbte_controller *out);
+int rtbte_set_controller(rtbte_ctx *ctx, int inst, const rtbte_controller *in);
 
 /* Linearised ph-ph scattering rates (the mode-resolved phonon rates used to converge grids,
  * Methods: computational details; Eq. ph-ph differentiated in the destination population):

@@ -33,7 +33,7 @@ RTBTE_RK4, RTBTE_BS32, RTBTE_ZON43, RTBTE_MRI_KW3, RTBTE_SPLIT_RK4 = 0, 1, 2, 3,
 HBAR_EV_PS = 6.582119569e-4
 
 EXPORTS = ["rtbte_desc_defaults", "rtbte_integ_defaults", "rtbte_create", "rtbte_upload_channels", "rtbte_rhs",
-           "rtbte_advance_to", "rtbte_phph_rates", "rtbte_get_sizes", "rtbte_download_channels", "rtbte_set_stream",
+           "rtbte_advance_to", "rtbte_get_controller", "rtbte_set_controller", "rtbte_phph_rates", "rtbte_get_sizes", "rtbte_download_channels", "rtbte_set_stream",
            "rtbte_autotune", "rtbte_get_tuning", "rtbte_set_graph_mode", "rtbte_set_kernel_timing", "rtbte_kernel_time", "rtbte_launch_count", "rtbte_last_error",
            "rtbte_status_string", "rtbte_eph_rhs_noalloc", "rtbte_surrogate_create", "rtbte_surrogate_collect",
            "rtbte_surrogate_train", "rtbte_surrogate_predict", "rtbte_surrogate_loss_grad",
@@ -75,7 +75,15 @@ class Integ(C.Structure):
                 ("a1", C.c_double), ("a2", C.c_double), ("a3", C.c_double), ("pid_sign_mode", C.c_int32),
                 ("max_nef", C.c_int32), ("safety", C.c_double), ("growth", C.c_double),
                 ("growth_first", C.c_double), ("etamxf", C.c_double), ("etamin", C.c_double),
-                ("small_nef", C.c_int32), ("chunk", C.c_int32)]
+                ("small_nef", C.c_int32), ("chunk", C.c_int32), ("resume", C.c_int32), ("reserved2", C.c_int32)]
+
+
+class Controller(C.Structure):
+    _fields_ = [("t", C.c_double), ("h", C.c_double), ("eps1", C.c_double), ("eps2", C.c_double),
+                ("first", C.c_int32), ("nef", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Stats(C.Structure):
@@ -116,6 +124,8 @@ def load():
         L.rtbte_rhs.argtypes = [vp, dbl, vp, vp, C.c_uint]
         L.rtbte_advance_to.argtypes = [vp, dbl, vp, vp, vp]
         L.rtbte_phph_rates.argtypes = [vp, vp, vp]
+        L.rtbte_get_controller.argtypes = [vp, i32, vp]
+        L.rtbte_set_controller.argtypes = [vp, i32, vp]
         L.rtbte_get_sizes.argtypes = [vp, i32, vp]
         L.rtbte_download_channels.argtypes = [vp, i32, C.c_uint, vp, vp, vp, vp]
         L.rtbte_set_stream.argtypes = [vp, vp]
@@ -328,6 +338,16 @@ class Context:
         d = st.as_dict()
         d["rc"] = rc
         return d
+
+    def get_controller(self, inst: int = 0) -> Controller:
+        """Step-size controller state of an instance (checkpointing)."""
+        c = Controller()
+        _check(self.ctx, load().rtbte_get_controller(self.ctx, inst, C.byref(c)))
+        return c
+
+    def set_controller(self, c: Controller, inst: int = 0):
+        """Restore a saved controller state; the next advance_to with resume=1 continues it."""
+        _check(self.ctx, load().rtbte_set_controller(self.ctx, inst, C.byref(c)))
 
     def phph_rates(self, y):
         """Linearised ph-ph rates -dI^{ph-ph}_a/dN_a on the sub-lattice rows (0 elsewhere)."""

@@ -379,6 +379,31 @@ int rtbte_rhs(rtbte_ctx *ctx, double t, const double *y, double *ydot, unsigned 
     return RTBTE_OK;
 }
 
+int rtbte_get_controller(const rtbte_ctx *ctx, int inst, rtbte_controller *out) {
+    if (!ctx || !out || inst < 0 || inst >= (int)ctx->inst.size()) return RTBTE_E_INVALID_ARG;
+    const Ctl &c = ctx->ctl_host[inst];
+    out->t = c.t;
+    out->h = c.h;
+    out->eps1 = c.eps1;
+    out->eps2 = c.eps2;
+    out->first = c.first;
+    out->nef = c.nef;
+    return RTBTE_OK;
+}
+
+int rtbte_set_controller(rtbte_ctx *ctx, int inst, const rtbte_controller *in) {
+    if (!ctx || !in || inst < 0 || inst >= (int)ctx->inst.size()) return RTBTE_E_INVALID_ARG;
+    if (!(in->h >= 0) || !(in->eps1 > 0) || !(in->eps2 > 0)) return fail(ctx, RTBTE_E_INVALID_ARG, "bad controller state");
+    Ctl &c = ctx->ctl_host[inst];
+    c.t = in->t;
+    c.h = in->h;
+    c.eps1 = in->eps1;
+    c.eps2 = in->eps2;
+    c.first = in->first;
+    c.nef = in->nef;
+    return RTBTE_OK;
+}
+
 int rtbte_phph_rates(rtbte_ctx *ctx, const double *y, double *rates) {
     if (!ctx) return RTBTE_E_INVALID_ARG;
     if (!y || !rates || !ptr_is_device(y) || !ptr_is_device(rates))

@@ -641,18 +641,33 @@ CtlParams ctl_params(const rtbte_integ *o, int p) {
     return cp;
 }
 
-void ctl_reset_all(rtbte_ctx *ctx, double t0, double t_out, long long max_steps) {
+// Fresh controllers for a call; with `keep`, the step proposal and error history of the
+// previous call (or of rtbte_set_controller) carry over.
+void ctl_reset_all(rtbte_ctx *ctx, double t0, double t_out, long long max_steps, bool keep = false) {
     for (int i = 0; i < n_inst(ctx); ++i) {
         Ctl *c = ctx->ctl_host + i;
-        const int cur = c->cur;
+        const Ctl prev = *c;
         std::memset(c, 0, sizeof(Ctl));
-        c->cur = cur;
+        c->cur = prev.cur;
         c->t = t0;
         c->t_out = t_out;
         c->eps1 = c->eps2 = 1.0;
         c->first = 1;
         c->max_steps = max_steps;
+        if (keep) {
+            c->h = prev.h;
+            c->eps1 = prev.eps1;
+            c->eps2 = prev.eps2;
+            c->first = prev.first;
+            c->nef = prev.nef;
+        }
     }
+}
+
+bool can_resume(rtbte_ctx *ctx) {
+    for (int i = 0; i < n_inst(ctx); ++i)
+        if (!(ctx->ctl_host[i].h > 0)) return false;
+    return true;
 }
 
 // Fixed-step RK4 of `parts` over [t0, t1] with nominal step h (last step ends at t1), every
@@ -716,7 +731,8 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
     const int NI = n_inst(ctx);
     for (int i = 0; i < NI; ++i) ctx->ctl_host[i].cur = 0;
     const long long max_steps = o->max_steps > 0 ? o->max_steps : 1000000000LL;
-    ctl_reset_all(ctx, o->t0, t_out, max_steps);
+    const bool resume = o->resume != 0 && can_resume(ctx);
+    ctl_reset_all(ctx, o->t0, t_out, max_steps, resume);
     int rc = RTBTE_OK;
     if (m == RTBTE_RK4) {
         if ((rc = write_ctl(ctx))) return rc;
@@ -728,8 +744,8 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
     } else if (m == RTBTE_BS32 || m == RTBTE_ZON43) {
         const Tableau T = tableau_of(m);
         CtlParams cp = ctl_params(o, T.p);
-        const bool est = !(o->h0 > 0);
-        if (!est)
+        const bool est = !resume && !(o->h0 > 0);
+        if (!est && !resume)
             for (int i = 0; i < NI; ++i) ctx->ctl_host[i].h = o->hmax > 0 && o->h0 > o->hmax ? o->hmax : o->h0;
         if ((rc = write_ctl(ctx))) return rc;
         if (est) {
@@ -749,7 +765,8 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
         const int fm = o->fast_method == RTBTE_BS32 ? RTBTE_BS32 : RTBTE_ZON43;
         const Tableau Tf = tableau_of(fm);
         CtlParams cp = ctl_params(o, Tf.p);
-        for (int i = 0; i < NI; ++i) ctx->ctl_host[i].h = 0.0;
+        if (!resume)
+            for (int i = 0; i < NI; ++i) ctx->ctl_host[i].h = 0.0;
         if ((rc = write_ctl(ctx))) return rc;
         const long long n = ctx->n_y;
         double *Fs = ctx->Fs.as<double>();
@@ -758,7 +775,7 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
         long long nsteps = (long long)ceil((t_out - o->t0) / o->h_s - 1e-9);
         if (nsteps < 1) nsteps = 1;
         double t = o->t0;
-        bool first_inner = true, failed = false;
+        bool first_inner = !resume, failed = false;
         long long inner_attempts = 0, inner_h0 = 0;
         StageArgs a = stage_args(ctx, Tf, cp, RTBTE_SLOW, nullptr);
         a.stage = -1;

@@ -429,3 +429,32 @@ def test_linearised_phph_rates_match_oracle(rt, oracle_lib, prec, tol):
         assert relL2(got, ref) < tol
         assert not got[ref == 0].any()
     ctx.close()
+
+
+@pytest.mark.parametrize("method", ["zon43", "mri"])
+def test_checkpoint_and_resume_continue_bit_for_bit(rt, method):
+    """Two calls in one context with resume=1 on the second (the controller's step proposal and
+    error history carry over) equal: first call, save (y, controller), destroy the context,
+    new context, restore, second call -- bit for bit, with the same step counts."""
+    m = ri.graphene_small(36)
+    kw = dict(rtol=1e-5, atol_c=1e-9, atol_ph=1e-12)
+    if method == "mri":
+        kw["h_s"] = 0.01
+    ctx = rt.Context(m)
+    ctx.upload_channels()
+    y = torch.tensor(m.y0(), device="cuda")
+    s1 = ctx.advance_to(0.02, y, method=method, t0=0.0, **kw)
+    y_mid = y.clone()
+    saved = ctx.get_controller()
+    s2 = ctx.advance_to(0.04, y, method=method, t0=0.02, resume=1, **kw)
+    assert s1["status"] == 0 and s2["status"] == 0
+    ctx.close()
+    ctx2 = rt.Context(m)
+    ctx2.upload_channels()
+    ctx2.set_controller(saved)
+    y2 = y_mid.clone()
+    s3 = ctx2.advance_to(0.04, y2, method=method, t0=0.02, resume=1, **kw)
+    ctx2.close()
+    assert torch.equal(y, y2)
+    assert (s2["steps"], s2["attempts"], s2["fails"]) == (s3["steps"], s3["attempts"], s3["fails"])
+    assert saved.h > 0 and saved.first == 0

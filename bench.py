@@ -52,8 +52,10 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-silicon", action="store_true")
     ap.add_argument("--accuracy-only", action="store_true", help="print only the error-versus-cost sweep")
     ap.add_argument("--surrogate-only", action="store_true", help="print only the learned slow-stage study")
+    ap.add_argument("--silicon-only", action="store_true", help="print only the silicon-like precision study")
     ap.add_argument("--direct-launches", action="store_true",
                     help="integrator attempts by direct kernel launches instead of the device-loop graph "
                          "(same kernels; for per-kernel launch lists)")
@@ -356,6 +358,79 @@ def accuracy_sweep(rt, ri, dev, t_end=0.5):
             "runs": runs, "sim_ps_per_s_at_1e-6": {k: t_end / v["seconds"] for k, v in best.items()}}
 
 
+def silicon_study(rt, ri, dev, n=32, t_end=0.5):
+    """Config 3 (reduced grids): the silicon-like 3D workload (three ellipsoidal conduction
+    bands on a 32^3 k-grid, fold 2, six branches on the 16^3 q-grid, ph-ph on the full q-grid,
+    where three-phonon processes dominate the stored entries).  Precision study: FP32
+    compensated collision sums against FP64 everywhere, each with FP64 state and controller,
+    errors at t_end against FP64 Zonneveld at rtol 1e-9; adaptive Zonneveld and MRI
+    (h_s = 50 fs, rtol 1e-5, atol_c 1e-9, atol_ph 1e-11)."""
+    import numpy as np
+    import torch
+
+    m = ri.silicon(n)
+    nc = m.n_c
+    y0 = torch.tensor(m.y0(), device=dev)
+    tol = dict(rtol=1e-5, atol_c=1e-9, atol_ph=1e-11)
+    out = {"workload": f"silicon-like 3D: 3 ellipsoidal conduction bands on {n}^3 k-grid within 0.4 eV "
+                       f"({nc} states), 6 branches on {n // 2}^3 q-grid ({m.n_ph} phonons), ph-ph on the full q-grid",
+           "t_end_ps": t_end}
+    ctxs = {}
+    for prec in ("fp32", "fp64"):
+        c = rt.Context(m, precision=prec, device=dev.index or 0)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        c.upload_channels()
+        torch.cuda.synchronize()
+        build_s = time.time() - t0
+        yd = torch.empty_like(y0)
+        c.rhs(y0, yd)
+        c.autotune(rt.RTBTE_ALL)
+        for _ in range(3):
+            c.rhs(y0, yd)
+        torch.cuda.synchronize()
+        c.set_kernel_timing(True)
+        c.kernel_time()
+        for _ in range(10):
+            c.rhs(y0, yd)
+        kms, kn = c.kernel_time()
+        c.set_kernel_timing(False)
+        sz = c.sizes(0)
+        ent = sz["eph_entries"] + sz["phe_entries"] + sz["pp_entries"]
+        bpe = 8 if prec == "fp32" else 12
+        out[prec] = {"channel_build_s": build_s, "entries": ent, "pp_entries": sz["pp_entries"],
+                     "rhs_kernel_ms": kms / kn, "achieved_gbs": bpe * ent / (kms / kn) / 1e6}
+        ctxs[prec] = c
+
+    def run(ctx, **kw):
+        y = y0.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        st = ctx.advance_to(t_end, y, t0=0.0, **kw)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        return y.cpu().numpy(), st, e0.elapsed_time(e1) / 1000.0
+
+    ref, st_ref, t_ref = run(ctxs["fp64"], method="zon43", rtol=1e-9, atol_c=1e-15, atol_ph=1e-15)
+    assert st_ref["status"] == 0, st_ref
+    runs = []
+    for prec in ("fp32", "fp64"):
+        for fam, kw in (("erk", dict(method="zon43", **tol)), ("mri", dict(method="mri", h_s=0.050, **tol))):
+            y, st, sec = run(ctxs[prec], **kw)
+            runs.append({"precision": prec, "method": fam, "status": st["status"], "seconds": sec,
+                         "sim_ps_per_s": t_end / sec,
+                         "err_carriers": float(np.linalg.norm(y[:nc] - ref[:nc]) / np.linalg.norm(ref[:nc])),
+                         "err_phonons": float(np.linalg.norm(y[nc:] - ref[nc:]) / np.linalg.norm(ref[nc:])),
+                         "steps": st["steps"], "rhs_full": st["rhs_full"], "rhs_fast": st["rhs_fast"],
+                         "rhs_slow": st["rhs_slow"]})
+    for c in ctxs.values():
+        c.close()
+    out["reference"] = {"method": "zon43", "precision": "fp64", "rtol": 1e-9, "seconds": t_ref, "steps": st_ref["steps"]}
+    out["runs"] = runs
+    return out
+
+
 def surrogate_study(rt, ri, dev, t_end=0.5, h_s=0.020, period=10):
     """The learned slow stage on the same workload and error protocol.  Pairs (N, exact
     I^{ph-ph}) come from the method's own trajectories (6 initial conditions, 21 states
@@ -591,6 +666,9 @@ def run_ours(args):
     # ---- learned slow stage (neural-operator surrogate of ph-ph inside MRI)
     surr = surrogate_study(rt, ri, dev) if (rank == 0 and not args.no_surrogate) else None
 
+    # ---- config 3: silicon-like 3D precision study
+    si = silicon_study(rt, ri, dev) if (rank == 0 and not args.no_silicon) else None
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -614,6 +692,7 @@ def run_ours(args):
                 "sim_ps_per_s_at_rel_err_1e-6": (max(acc["sim_ps_per_s_at_1e-6"].values())
                                                  if acc and acc["sim_ps_per_s_at_1e-6"] else None),
                 "roofline": roofline, "e2e": e2e, "mri": mri, "accuracy": acc, "ensemble": ens, "surrogate": surr,
+                "silicon": si,
                 "clocks": clk.summary(),
                 "gpu_launches": launches,
                 "cpu_baseline": cpu}
@@ -635,6 +714,14 @@ def main():
         import rtbte_inputs as ri
 
         print(json.dumps(accuracy_sweep(rt, ri, torch.device("cuda", 0))), flush=True)
+        return 0
+    if args.silicon_only:
+        import torch
+
+        import paper_2412_13402_gb300 as rt
+        import rtbte_inputs as ri
+
+        print(json.dumps(silicon_study(rt, ri, torch.device("cuda", 0))), flush=True)
         return 0
     if args.surrogate_only:
         import torch

@@ -192,6 +192,8 @@ typedef struct rtbte_stats {
     int32_t surrogate_fallbacks;         /* MRI calls that detached the surrogate (0/1)   */
     int64_t slow_exact, slow_surrogate;  /* MRI slow stages: exact / surrogate values     */
     double judge_err_max;                /* largest relative error seen by a judge (or -1)*/
+    int64_t range_violations;            /* rows of accepted step states with f outside
+                                            [-atol_c, 1+atol_c] or N < -atol_ph           */
 } rtbte_stats;
 
 typedef struct rtbte_ctx rtbte_ctx;

@@ -91,7 +91,7 @@ class Stats(C.Structure):
                 ("rhs_fast", C.c_int64), ("rhs_slow", C.c_int64), ("slow_steps", C.c_int64), ("t", C.c_double),
                 ("h_last", C.c_double), ("h_next", C.c_double), ("status", C.c_int32),
                 ("surrogate_fallbacks", C.c_int32), ("slow_exact", C.c_int64), ("slow_surrogate", C.c_int64),
-                ("judge_err_max", C.c_double)]
+                ("judge_err_max", C.c_double), ("range_violations", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

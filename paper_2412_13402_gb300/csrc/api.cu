@@ -4,9 +4,17 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.cuh"
 
 namespace rtbte {
+
+// NVTX range over a public call (visible to profilers; no cost without a tool attached)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 int fail(rtbte_ctx *ctx, int code, const std::string &msg) {
     if (ctx) ctx->err = msg;
@@ -330,7 +338,8 @@ int rtbte_create(const rtbte_desc *d, rtbte_ctx **out) {
         (rc = dev_alloc(ctx, ctx->Fs, sizeof(double) * y * 3, true)) ||
         (rc = dev_alloc(ctx, ctx->forcing, sizeof(double) * y, true)) ||
         (rc = dev_alloc(ctx, ctx->wrms_part, sizeof(double) * (2 * y + 2LL * kWrmsChunks * d->n_instances), true)) ||
-        (rc = dev_alloc(ctx, ctx->ctl, sizeof(Ctl) * d->n_instances, true)))
+        (rc = dev_alloc(ctx, ctx->ctl, sizeof(Ctl) * d->n_instances, true)) ||
+        (rc = dev_alloc(ctx, ctx->range_scratch, sizeof(unsigned long long) * d->n_instances, true)))
         return bail(rc);
     if (cudaMallocHost(&ctx->ctl_host, sizeof(Ctl) * d->n_instances) != cudaSuccess)
         return bail(cuda_fail(ctx, cudaErrorMemoryAllocation, "cudaMallocHost"));
@@ -342,6 +351,7 @@ int rtbte_create(const rtbte_desc *d, rtbte_ctx **out) {
 }
 
 int rtbte_upload_channels(rtbte_ctx *ctx, int inst, const rtbte_channels *ch) {
+    Range nvtx_range("rtbte_upload_channels");
     if (!ctx) return RTBTE_E_INVALID_ARG;
     if (!ch || inst < 0 || inst >= (int)ctx->inst.size()) return fail(ctx, RTBTE_E_INVALID_ARG, "bad instance or channels");
     InstHost &I = ctx->inst[inst];
@@ -355,6 +365,7 @@ int rtbte_upload_channels(rtbte_ctx *ctx, int inst, const rtbte_channels *ch) {
 }
 
 int rtbte_rhs(rtbte_ctx *ctx, double t, const double *y, double *ydot, unsigned parts) {
+    Range nvtx_range("rtbte_rhs");
     (void)t;
     if (!ctx) return RTBTE_E_INVALID_ARG;
     if (!y || !ydot || parts == 0 || parts > RTBTE_ALL) return fail(ctx, RTBTE_E_INVALID_ARG, "bad rhs arguments");
@@ -405,6 +416,7 @@ int rtbte_set_controller(rtbte_ctx *ctx, int inst, const rtbte_controller *in) {
 }
 
 int rtbte_phph_rates(rtbte_ctx *ctx, const double *y, double *rates) {
+    Range nvtx_range("rtbte_phph_rates");
     if (!ctx) return RTBTE_E_INVALID_ARG;
     if (!y || !rates || !ptr_is_device(y) || !ptr_is_device(rates))
         return fail(ctx, RTBTE_E_INVALID_ARG, "y and rates must be device pointers");
@@ -418,6 +430,7 @@ int rtbte_phph_rates(rtbte_ctx *ctx, const double *y, double *rates) {
 }
 
 int rtbte_advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *opt, rtbte_stats *st) {
+    Range nvtx_range("rtbte_advance_to");
     if (!ctx) return RTBTE_E_INVALID_ARG;
     if (!y || !opt) return fail(ctx, RTBTE_E_INVALID_ARG, "bad advance_to arguments");
     if (!ptr_is_device(y)) return fail(ctx, RTBTE_E_INVALID_ARG, "y must be a device pointer");
@@ -469,6 +482,7 @@ int rtbte_set_stream(rtbte_ctx *ctx, void *stream) {
 }
 
 int rtbte_autotune(rtbte_ctx *ctx, unsigned parts, int *chosen) {
+    Range nvtx_range("rtbte_autotune");
     if (!ctx) return RTBTE_E_INVALID_ARG;
     if (parts == 0 || parts > RTBTE_ALL) return fail(ctx, RTBTE_E_INVALID_ARG, "bad parts");
     int rc;
@@ -553,7 +567,8 @@ void rtbte_destroy(rtbte_ctx *ctx) {
     ctx->tail_ctr.release();
     DevBuf *bufs[] = {&ctx->popf, &ctx->popN, &ctx->popP, &ctx->instdev, &ctx->compact, &ctx->items, &ctx->groups,
                       &ctx->partials, &ctx->eoff, &ctx->poff, &ctx->ppoff, &ctx->cta_tab, &ctx->wpre, &ctx->dyn_tab, &ctx->Y[0], &ctx->Y[1],
-                      &ctx->K, &ctx->Fs, &ctx->forcing, &ctx->wrms_part, &ctx->ctl, &ctx->ystage, &ctx->ydstage};
+                      &ctx->K, &ctx->Fs, &ctx->forcing, &ctx->wrms_part, &ctx->ctl, &ctx->ystage, &ctx->ydstage,
+                      &ctx->range_scratch};
     for (DevBuf *b : bufs) b->release();
     for (auto &pr : ctx->ev_pending) {
         ctx->ev_pool.push_back(pr.first);

@@ -90,6 +90,7 @@ struct StageArgs {
     double *Y0, *Y1, *K;
     const double *forcing;
     double *wsq;  // per-row squared weighted error of the last stage
+    unsigned long long *range;  // per instance: rows of the attempted state out of range
     long long n;
     unsigned parts;
     int stage;         // -1: populations <- y; 0..S-1: combine stage `stage`
@@ -131,6 +132,10 @@ __global__ void __launch_bounds__(kRedThreads) stage_kernel(RowParams Q, StageAr
             }
             const double ynew = y[c] + h * s1;
             (C->cur ? a.Y0 : a.Y1)[c] = ynew;
+            // populations outside their physical range (f in [0,1], N >= 0) beyond the absolute
+            // tolerance: counted per attempt, added to the instance's total if it is accepted
+            const bool out = local < I.n_c ? (ynew < -a.cp.atol_c || ynew > 1.0 + a.cp.atol_c) : (ynew < -a.cp.atol_ph);
+            if (out && a.range) atomicAdd(a.range + ii, 1ULL);
             double x2 = 0.0;
             if (a.T.has_emb) {  // error weight in precision R (a relative 1e-7 in the norm is immaterial)
                 const double e = h * s2;
@@ -191,13 +196,16 @@ __global__ void wrms_chunks(RowParams Q, const Ctl *ctl, const double *wsq, doub
     if (threadIdx.x == 0) part[(long long)i * gridDim.x + blockIdx.x] = s;
 }
 
-__global__ void controller_kernel(RowParams Q, Ctl *ctl, CtlParams cp, const double *part) {
+__global__ void controller_kernel(RowParams Q, Ctl *ctl, CtlParams cp, const double *part,
+                                  unsigned long long *range) {
     Ctl *c = ctl + blockIdx.x;
     if (c->done) return;
     const InstDev I = Q.inst[blockIdx.x];
     const long long ni = (long long)I.n_c + I.n_ph;
     const double sum = block_sum(part, (long long)blockIdx.x * kWrmsChunks, kWrmsChunks);
     if (threadIdx.x != 0) return;
+    const unsigned long long nr = range[blockIdx.x];
+    range[blockIdx.x] = 0;
     const double eps = sqrt(sum / (double)ni);
     c->attempts++;
     if (!isfinite(eps)) {
@@ -209,6 +217,7 @@ __global__ void controller_kernel(RowParams Q, Ctl *ctl, CtlParams cp, const dou
         c->cur ^= 1;
         c->t = c->last ? c->t_out : c->t + c->h_try;
         c->steps++;
+        c->range_viol += (long long)nr;
         c->h_last = c->h_try;
         if (c->last) c->done = 1;
         else arm(c);
@@ -220,6 +229,7 @@ __global__ void controller_kernel(RowParams Q, Ctl *ctl, CtlParams cp, const dou
         c->cur ^= 1;
         c->t = c->last ? c->t_out : c->t + c->h_try;
         c->steps++;
+        c->range_viol += (long long)nr;
         const double e = eps > 1e-10 ? eps : 1e-10;
         double eta = cp.pid_sign_mode == 0 ? pow(e, -cp.a1 / p) * pow(c->eps1, cp.a2 / p) * pow(c->eps2, -cp.a3 / p)
                                            : pow(e, -cp.a1 / p) * pow(c->eps1, -cp.a2 / p) * pow(c->eps2, -cp.a3 / p);
@@ -396,6 +406,7 @@ StageArgs stage_args(rtbte_ctx *ctx, const Tableau &T, const CtlParams &cp, unsi
     a.Y0 = ctx->Y[0].as<double>();
     a.Y1 = ctx->Y[1].as<double>();
     a.K = ctx->K.as<double>();
+    a.range = ctx->range_scratch.as<unsigned long long>();
     a.forcing = forcing;
     a.wsq = ctx->wrms_part.as<double>();
     a.n = ctx->n_y;
@@ -419,7 +430,8 @@ int enqueue_attempt(rtbte_ctx *ctx, const Tableau &T, const CtlParams &cp, unsig
     double *chunks = ctx->wrms_part.as<double>() + 2 * ctx->n_y;
     wrms_chunks<<<dim3(kWrmsChunks, n_inst(ctx)), kRedThreads, 0, s>>>(row_params(ctx), ctx->ctl.as<Ctl>(),
                                                                       ctx->wrms_part.as<double>(), chunks, 1);
-    controller_kernel<<<n_inst(ctx), kRedThreads, 0, s>>>(row_params(ctx), ctx->ctl.as<Ctl>(), cp, chunks);
+    controller_kernel<<<n_inst(ctx), kRedThreads, 0, s>>>(row_params(ctx), ctx->ctl.as<Ctl>(), cp, chunks,
+                                                          ctx->range_scratch.as<unsigned long long>());
     RT_CUDA(ctx, cudaGetLastError());
     ctx->launches += 2;
     return RTBTE_OK;
@@ -703,6 +715,9 @@ void gather_stats(rtbte_ctx *ctx, rtbte_stats *st, bool add_steps) {
         if (c.t < t) t = c.t;
         if (status == RTBTE_OK && c.status != RTBTE_OK) status = c.status;
     }
+    long long rv = 0;
+    for (int i = 0; i < n_inst(ctx); ++i) rv += ctx->ctl_host[i].range_viol;
+    st->range_violations = add_steps ? st->range_violations + rv : rv;
     st->steps = add_steps ? st->steps + steps : steps;
     st->fails += fails;
     st->t = t;

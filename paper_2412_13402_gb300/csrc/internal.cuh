@@ -83,7 +83,7 @@ struct __align__(16) Ctl {
     double eps, eps1, eps2, h_last;
     double h0tmp, span_t0, pad_d0, pad_d1;
     long long steps, attempts, fails, rhs;
-    long long max_steps, steps_base, pad_l0, pad_l1;
+    long long max_steps, steps_base, range_viol, pad_l1;  // range_viol: out-of-range rows in accepted steps
     int first, nef, done, status;
     int cur, last, fixed, pad_i0;
 };
@@ -208,7 +208,7 @@ struct rtbte_ctx {
     int num_sms = 0;
     size_t smem_optin = 0;
     // integrator work buffers
-    rtbte::DevBuf Y[2], K, Fs, forcing, wrms_part, ctl, ystage, ydstage;  // wrms_part: 2 x n_y squared norms, then per-instance chunk sums
+    rtbte::DevBuf Y[2], K, Fs, forcing, wrms_part, ctl, ystage, ydstage, range_scratch;  // wrms_part: 2 x n_y squared norms, then per-instance chunk sums
     rtbte::Ctl *ctl_host = nullptr;  // pinned mirror of the per-instance controllers
     std::map<long long, cudaGraphExec_t> graphs;
     std::map<long long, int> graph_launches;  // kernels per attempt of each attempt-loop graph

@@ -364,6 +364,51 @@ def tiny(n=(4, 4, 1), nbands: int = 2, nmodes: int = 3, fold: int = 1, pp_stride
     )
 
 
+SILICON_MODES = (("TA1", "ac", 0.020), ("TA2", "ac", 0.022), ("LA", "ac", 0.050),
+                  ("TO1", "op", 0.060), ("TO2", "op", 0.061), ("LO", "op", 0.063))
+
+
+def silicon(n: int = 32, fold: int = 2, window: float = 0.4, seed: int = SEED_BASE + 2, T: float = 300.0,
+            E_x: float = 0.2, amp: float = 0.2, width: float = 0.03, sigma_eph: float | None = None,
+            sigma_pp: float | None = None, v3_coef: float = 2.0e-8) -> Model:
+    """Bulk-silicon-like 3D model (the precision-study workload): three conduction bands, band b
+    being the pair of ellipsoidal valleys on axis b at +-0.85 of the zone half-width (m_l = 0.92,
+    m_t = 0.19, lattice 5.43 Angstrom, simple cubic zone), states within `window` of the band
+    minimum on an n^3 k-grid; six phonon branches (two TA and one LA Debye-like acoustic, three
+    flat ~60 meV optical) on the (n/fold)^3 q-grid, ph-ph on the full q-grid; hot electrons
+    at E_x over a 300 K Fermi-Dirac tail.  Broadenings default to the paper's 5 meV and 1.1 meV
+    scaled by 80/n and 40/(n/fold) so that coarse grids keep resonant channels."""
+    nk = (n, n, n)
+    nq = tuple(x // fold for x in nk)
+    a = 5.43
+    dk = (2 * np.pi / (n * a),) * 3
+    k0 = 0.85 * np.pi / a  # valley centre on its axis
+
+    def eps_fn(b, c):
+        k = _kvec(c, nk, dk)
+        kl = np.abs(k[:, b]) - k0
+        kt2 = sum(k[:, ax] ** 2 for ax in range(3) if ax != b)
+        return HB2_2ME * (kl ** 2 / 0.92 + kt2 / 0.19)
+
+    e_band, e_k, e_eps = _electron_states(nk, 3, eps_fn, lambda b, e: e <= window)
+    s = _shape_s(nq, 3)
+    om = [w * s if kind == "ac" else w - 0.004 * s * s for _, kind, w in SILICON_MODES]
+    omega = np.concatenate(om)
+    f0 = fermi_dirac(e_eps, -0.15, T) + amp * np.exp(-((e_eps - E_x) ** 2) / (2 * width ** 2))
+    N0 = bose_einstein(omega, T)
+    N0[omega < 0.0002] = 0.0
+    return Model(
+        name=f"silicon_{n}_f{fold}", dim=3, nk=nk, nq=nq, fold=fold, nbands=3,
+        e_band=e_band, e_k=e_k, e_eps=e_eps, nmodes=6, ph_omega=omega, pp_stride=1,
+        sigma_eph=0.005 * 80.0 / n if sigma_eph is None else sigma_eph,
+        sigma_pp=0.0011 * 40.0 / nq[0] if sigma_pp is None else sigma_pp, omega_cut=0.0002,
+        g2_seed=seed, v3_seed=seed + 1000003, g2_coef=np.full(6, 1e-3), v3_coef=v3_coef,
+        lut_bits=12, lut=lognormal_lut(12, 1.0), f0=np.ascontiguousarray(f0), N0=N0,
+        integ=dict(t_end=20.0, h_s=0.050, rtol=1e-5, atol_c=1e-9, atol_ph=1e-11),
+        note="config 3: silicon-like 3D, precision study (reduced grids)",
+    )
+
+
 def ensemble(n_inst: int = 64, seed: int = SEED_BASE + 3, sides=tuple(range(24, 97, 3))) -> list:
     """Batched ensemble: independent graphene-like instances with uneven grids (side drawn
     uniformly from `sides`), excitation energies E_x ~ U[0.1, 1.0] eV and temperatures
@@ -395,5 +440,5 @@ def random_populations(model: Model, seed: int, spread: float = 1.0):
 
 def by_name(name: str, **kw) -> Model:
     table = {"toy2d": toy2d, "graphene": graphene, "graphene_small": graphene_small,
-             "ladder": ladder, "tiny": tiny}
+             "ladder": ladder, "tiny": tiny, "silicon": silicon}
     return table[name](**kw)

@@ -73,6 +73,7 @@ MODELS = {
     "toy2d": lambda: ri.toy2d(),
     "ladder": lambda: ri.ladder(n=6),
     "graphene36": lambda: ri.graphene_small(36),
+    "silicon16": lambda: ri.silicon(16),
 }
 
 
@@ -105,7 +106,7 @@ def test_channel_lists_match_oracle(rt, oracle_lib, name, prec):
 
 @pytest.mark.parametrize("parts", [ALL, EPH, PHE, PHPH, FAST])
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp64", 1e-12)])
-@pytest.mark.parametrize("name", ["tiny3d_fold2", "tiny2d_pp2", "toy2d", "graphene36"])
+@pytest.mark.parametrize("name", ["tiny3d_fold2", "tiny2d_pp2", "toy2d", "graphene36", "silicon16"])
 def test_rhs_matches_oracle(rt, oracle_lib, name, prec, tol, parts):
     m = MODELS[name]()
     ctx = rt.Context(m, precision=prec)
@@ -458,3 +459,21 @@ def test_checkpoint_and_resume_continue_bit_for_bit(rt, method):
     assert torch.equal(y, y2)
     assert (s2["steps"], s2["attempts"], s2["fails"]) == (s3["steps"], s3["attempts"], s3["fails"])
     assert saved.h > 0 and saved.first == 0
+
+
+def test_population_range_violations_are_counted(rt):
+    """Accepted step states with an occupation above 1 (beyond atol_c) are reported in
+    rtbte_stats.range_violations; a physical start reports none."""
+    m = ri.toy2d()
+    ctx = rt.Context(m, precision="fp64")
+    ctx.upload_channels()
+    y = torch.tensor(m.y0(), device="cuda")
+    st = ctx.advance_to(0.005, y, method="rk4", t0=0.0, h=0.001)
+    assert st["status"] == 0 and st["range_violations"] == 0
+    y0 = m.y0()
+    y0[:3] = 1.5  # three electron states overfilled; two short steps keep them above 1
+    y = torch.tensor(y0, device="cuda")
+    st = ctx.advance_to(2e-5, y, method="rk4", t0=0.0, h=1e-5)
+    assert st["status"] == 0 and st["steps"] == 2
+    assert (y[:3] > 1.0).all() and st["range_violations"] == 6
+    ctx.close()

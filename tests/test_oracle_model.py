@@ -49,3 +49,19 @@ def test_initial_states_are_inversion_symmetric():
         for nu in range(m.nmodes):
             assert np.array_equal(m.N0[nu * m.N_q + q], m.N0[nu * m.N_q + qi])
             assert np.array_equal(m.ph_omega[nu * m.N_q + q], m.ph_omega[nu * m.N_q + qi])
+
+
+def test_silicon_like_model_shape(oracle_lib):
+    """The silicon-like 3D model (fold 2): states within the 0.4 eV window of three ellipsoidal
+    valley pairs, each band holding both valleys of its axis in equal numbers; ph-ph channels
+    exist on the full q-grid (carrier conservation is checked with the other models)."""
+    m = ri.silicon(16)
+    assert m.dim == 3 and m.fold == 2 and m.nq == (8, 8, 8)
+    assert (m.e_eps <= 0.4).all() and (m.e_eps >= 0).all()
+    assert sorted(set(m.e_band.tolist())) == [0, 1, 2]
+    for b in range(3):
+        kb = m.e_k[m.e_band == b][:, b]
+        lo = (kb < m.nk[b] // 2).sum()
+        assert lo > 0 and abs(2 * lo - kb.shape[0]) <= kb.shape[0] // 4
+    o = oracle_lib.Oracle(m)
+    assert o.pp_lists()["off"][-1] > 0

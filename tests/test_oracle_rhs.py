@@ -117,7 +117,7 @@ def test_detailed_balance_exact_resonance(oracle_lib, T, mu):
 # Conservation laws
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("mk", [lambda: ri.toy2d(), lambda: ri.graphene_small(24),
-                                lambda: ri.tiny((4, 4, 4), fold=2, nbands=2, nmodes=2)])
+                                lambda: ri.tiny((4, 4, 4), fold=2, nbands=2, nmodes=2), lambda: ri.silicon(16)])
 def test_carrier_number_conservation(oracle_lib, mk):
     m = mk()
     o = oracle_lib.Oracle(m)

@@ -38,10 +38,9 @@ constexpr int kWrmsChunks = 128;  // per-instance blocks of the WRMS reduction b
 constexpr int kLoopCap = 64;     // attempts per launch of an attempt-loop graph (default)
 
 enum { PART_EPH = 0, PART_PHE = 1, PART_PP = 2 };
-// Lanes working on one item: an item holds at most 16 x kItemLanes entries and a warp works on
-// 32 / kItemLanes items at a time (16 and 8 lanes, which pack short segments together, measured
-// slower on the graphene-like workload than whole-warp items).
-constexpr int kItemLanes = 32;
+// Lanes working on one item are chosen per staging group (Group::lanes_log2): 8, 16 or 32 lanes,
+// items of at most 16 x lanes entries, so that groups of short segments pack several items into
+// one warp while groups of long segments keep whole-warp items.
 
 
 struct __align__(16) Item {
@@ -59,6 +58,7 @@ struct __align__(16) Group {
     int item_begin, item_end;
     int part, inst, nu, s_bits;
     int pp_bits, n_q_pad;
+    int lanes_log2, pad_g;       // lanes per item = 1 << lanes_log2 (3, 4 or 5)
     int stage0_len, stage1_len;  // staged element counts (multiples of 4)
     long long stage0_src;        // popf (e-ph, ph-e) or popP (ph-ph) offset of the staged block
     long long stage1_src;        // popN offset of the staged mode slice (e-ph)
@@ -205,6 +205,7 @@ struct rtbte_ctx {
     double part_scale[3] = {1.0, 1.0, 1.0};  // relative cost of an entry of each part
     size_t smem_bytes = 0;
     bool staged = false;
+    bool wide = true;  // every group uses whole-warp items (the kernel variant without sub-warps)
     int num_sms = 0;
     size_t smem_optin = 0;
     // integrator work buffers

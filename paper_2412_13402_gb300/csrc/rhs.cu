@@ -5,8 +5,10 @@
 // cache-streaming loads, 4 entries per lane), while the populations they gather are
 // staged per CTA in shared memory: the instance's electron occupations f plus, for e-ph
 // work, the occupations N of one phonon mode (the e-ph lists are blocked by mode for this
-// reason); for ph-e work only f; for ph-ph work the sub-lattice N.  Each warp owns one
-// work item (<= 512 entries of a single destination segment), accumulates it per lane with
+// reason); for ph-e work only f; for ph-ph work the sub-lattice N.  A work item is a piece
+// of a single destination segment; groups of long segments give each warp one item of up to
+// 512 entries, groups of short ones give each sub-warp of 8 or 16 lanes one item of up to 128
+// or 256 entries.  Lanes accumulate their entries with
 // compensated (two-sum) additions and adds the lanes with a shuffle tree; the partial is
 // written per item, and the row kernels add partials in item order (deterministic).  CTAs
 // first run a static share of the items (split by estimated cost), then take the rest in
@@ -74,23 +76,24 @@ template <class R> struct GroupView {
     const R *s0, *s1;  // staged (or global) populations: e-ph f & N of one mode, ph-e f, ph-ph N
     const R *Nglob;    // instance phonon populations (ph-e destinations)
     int part, sb, pb;
+    int lg;  // lanes per item = 1 << lg
 };
 
-// Entry loads of one item on a sub-warp of SW lanes: VPL vectors of 4 entries per lane
+// Entry loads of one item on a sub-warp of 1 << lg lanes: VPL vectors of 4 entries per lane
 // (16-byte streaming loads); sl is the lane's index in its sub-warp.
-template <class R, int VPL, int SW> struct Batch;
-template <int VPL, int SW> struct Batch<float, VPL, SW> {
+template <class R, int VPL> struct Batch;
+template <int VPL> struct Batch<float, VPL> {
     uint4 iv[VPL];
     float4 wv[VPL];
     float Np;  // ph-e destination population, loaded with the entries
-    __device__ __forceinline__ void issue(const GroupView<float> &V, const Item &it, int sl) {
+    __device__ __forceinline__ void issue(const GroupView<float> &V, const Item &it, int sl, int lg) {
         const int nv = it.len >> 2;
         if (V.part == PART_PHE) Np = V.Nglob[it.dest];
         const uint4 *ip = reinterpret_cast<const uint4 *>(V.idx + it.begin);
         const float4 *wp = reinterpret_cast<const float4 *>(V.W + it.begin);
 #pragma unroll
         for (int j = 0; j < VPL; ++j) {
-            const int v = sl + SW * j;
+            const int v = sl + (j << lg);
             if (v < nv) {
                 iv[j] = __ldcs(ip + v);
                 wv[j] = __ldcs(wp + v);
@@ -101,18 +104,18 @@ template <int VPL, int SW> struct Batch<float, VPL, SW> {
         return k == 0 ? wv[j].x : k == 1 ? wv[j].y : k == 2 ? wv[j].z : wv[j].w;
     }
 };
-template <int VPL, int SW> struct Batch<double, VPL, SW> {
+template <int VPL> struct Batch<double, VPL> {
     uint4 iv[VPL];
     double2 wa[VPL], wb[VPL];
     double Np;  // ph-e destination population, loaded with the entries
-    __device__ __forceinline__ void issue(const GroupView<double> &V, const Item &it, int sl) {
+    __device__ __forceinline__ void issue(const GroupView<double> &V, const Item &it, int sl, int lg) {
         const int nv = it.len >> 2;
         if (V.part == PART_PHE) Np = V.Nglob[it.dest];
         const uint4 *ip = reinterpret_cast<const uint4 *>(V.idx + it.begin);
         const double2 *wp = reinterpret_cast<const double2 *>(V.W + it.begin);
 #pragma unroll
         for (int j = 0; j < VPL; ++j) {
-            const int v = sl + SW * j;
+            const int v = sl + (j << lg);
             if (v < nv) {
                 iv[j] = __ldcs(ip + v);
                 wa[j] = __ldcs(wp + 2 * v);
@@ -132,9 +135,9 @@ __device__ __forceinline__ unsigned comp4(const uint4 &e, int k) {
 // Per-lane sum of W*F over one item: each 4-entry vector is summed with an FMA chain and the
 // vector sums are added with two-sum into (acc, cmp); the warp reduction is done later for
 // four items at once (Pending).
-template <class R, int VPL, int SW>
-__device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &it, const Batch<R, VPL, SW> &b, int sl,
-                                             R &acc, R &cmp) {
+template <class R, int VPL>
+__device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &it, const Batch<R, VPL> &b, int sl,
+                                             int lg, R &acc, R &cmp) {
     const int nv = it.len >> 2;
     acc = R(0);
     cmp = R(0);
@@ -144,7 +147,7 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
         if (it.proc == 0) {  // F_em = f(1-f') + N(f-f') = fma(N, f-f', fma(f', -f, f))
 #pragma unroll
             for (int j = 0; j < VPL; ++j) {
-                if (sl + SW * j >= nv) continue;
+                if (sl + (j << lg) >= nv) continue;
                 R t = R(0);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -159,7 +162,7 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
             const R u = R(1) - fd;
 #pragma unroll
             for (int j = 0; j < VPL; ++j) {
-                if (sl + SW * j >= nv) continue;
+                if (sl + (j << lg) >= nv) continue;
                 R t = R(0);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -176,7 +179,7 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
         const R Np = b.Np;
 #pragma unroll
         for (int j = 0; j < VPL; ++j) {
-            if (sl + SW * j >= nv) continue;
+            if (sl + (j << lg) >= nv) continue;
             R t = R(0);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -193,7 +196,7 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
         if (it.proc == 0) {  // G_em = N(N'+N''+1) - N'N''
 #pragma unroll
             for (int j = 0; j < VPL; ++j) {
-                if (sl + SW * j >= nv) continue;
+                if (sl + (j << lg) >= nv) continue;
                 R t = R(0);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -207,7 +210,7 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
         } else {  // G_abs = N(N''-N') - N'(N''+1)
 #pragma unroll
             for (int j = 0; j < VPL; ++j) {
-                if (sl + SW * j >= nv) continue;
+                if (sl + (j << lg) >= nv) continue;
                 R t = R(0);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -315,12 +318,13 @@ __device__ __forceinline__ void prefetch_item(const GroupView<R> &V, const DescS
 // sub-warp by a butterfly in a fixed order (every lane ends with the same bits).  The RHS error
 // is set by the conversion of the populations to FP32 (about 5e-8 relative on the parity
 // models), not by this tree: the compensated tree measured the same to two digits.
-template <class R, int SW>
-__device__ __forceinline__ void finish_item(const KParams &P, int k, bool valid, R acc, R cmp, int sl) {
+template <class R>
+__device__ __forceinline__ void finish_item(const KParams &P, int k, bool valid, R acc, R cmp, int sl, int lg) {
     acc += cmp;
     cmp = R(0);
 #pragma unroll
-    for (int o = SW / 2; o; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    for (int o = 16; o; o >>= 1)
+        if (o < (1 << lg)) acc += __shfl_xor_sync(kFull, acc, o);
     if (sl == 0 && valid) {
         R *out = reinterpret_cast<R *>(P.partials) + 2LL * k;
         out[0] = acc;
@@ -328,19 +332,22 @@ __device__ __forceinline__ void finish_item(const KParams &P, int k, bool valid,
     }
 }
 
-// Items a, a+st, a+2st, ... < b of one group for one warp.  The warp works on 32/SW items at
-// a time, one per sub-warp of SW lanes (items of the part are cut to at most 16*SW entries:
-// short ph-e segments pack four to a warp).  With PIPE, the next items' entry loads are in
-// flight while the current ones are computed (two register buffers).
-template <class R, bool PIPE, int SW>
+// Items a, a+st, a+2st, ... < b of one group for one warp.  The warp works on G = 32 >> lg
+// items at a time, one per sub-warp of 1 << lg lanes (the group's items are cut to at most
+// 16 << lg entries, so groups of short segments pack two or four items to a warp).  WIDE is
+// the variant for plans whose groups all use whole-warp items (lg = 5 at compile time).  With
+// PIPE, the next items' entry loads are in flight while the current ones are computed (two
+// register buffers).
+template <class R, bool PIPE, bool WIDE>
 __device__ __forceinline__ void run_range(const KParams &P, const GroupView<R> &V, int a, int b, int st, int lane) {
     if (a >= b) return;
-    constexpr int G = 32 / SW;
-    const int h = lane / SW, sl = lane & (SW - 1);
+    const int lg = WIDE ? 5 : V.lg;
+    const int G = 32 >> lg;
+    const int h = lane >> lg, sl = lane & ((1 << lg) - 1);
     DescStream D;
     D.init(P.items, a, b, st, lane);
-    auto next = [&](int kb) { return G == 1 ? D.get(kb, lane) : D.get_sub(kb, h); };
-    auto valid = [&](int kb) { return G == 1 || kb + h * st < b; };
+    auto next = [&](int kb) { return WIDE ? D.get(kb, lane) : D.get_sub(kb, h); };
+    auto valid = [&](int kb) { return WIDE || kb + h * st < b; };
     const int pf = P.pf_dist;  // iterations ahead whose entries are prefetched into L2 (0: none)
     R acc, cmp;
     if (pf > 0)
@@ -349,37 +356,37 @@ __device__ __forceinline__ void run_range(const KParams &P, const GroupView<R> &
         for (int k = a; k < b; k += G * st) {
             const Item it = next(k);
             if (pf > 0) prefetch_item(V, D, k + pf * G * st, b, lane);
-            Batch<R, 4, SW> B;
-            B.issue(V, it, sl);
-            compute_item<R, 4, SW>(V, it, B, sl, acc, cmp);
-            finish_item<R, SW>(P, k + h * st, valid(k), acc, cmp, sl);
+            Batch<R, 4> B;
+            B.issue(V, it, sl, lg);
+            compute_item<R, 4>(V, it, B, sl, lg, acc, cmp);
+            finish_item<R>(P, k + h * st, valid(k), acc, cmp, sl, lg);
         }
         return;
     }
-    Batch<R, 4, SW> A, B;
+    Batch<R, 4> A, B;
     int k = a;
     Item ia = next(k);
-    A.issue(V, ia, sl);
+    A.issue(V, ia, sl, lg);
     for (;;) {
         const bool hb = k + G * st < b;
         Item ib;
         if (hb) {
             ib = next(k + G * st);
-            B.issue(V, ib, sl);
+            B.issue(V, ib, sl, lg);
         }
         if (pf > 0) prefetch_item(V, D, k + pf * G * st, b, lane);
-        compute_item<R, 4, SW>(V, ia, A, sl, acc, cmp);
-        finish_item<R, SW>(P, k + h * st, valid(k), acc, cmp, sl);
+        compute_item<R, 4>(V, ia, A, sl, lg, acc, cmp);
+        finish_item<R>(P, k + h * st, valid(k), acc, cmp, sl, lg);
         if (!hb) break;
         k += G * st;
         const bool ha = k + G * st < b;
         if (ha) {
             ia = next(k + G * st);
-            A.issue(V, ia, sl);
+            A.issue(V, ia, sl, lg);
         }
         if (pf > 0) prefetch_item(V, D, k + pf * G * st, b, lane);
-        compute_item<R, 4, SW>(V, ib, B, sl, acc, cmp);
-        finish_item<R, SW>(P, k + h * st, valid(k), acc, cmp, sl);
+        compute_item<R, 4>(V, ib, B, sl, lg, acc, cmp);
+        finish_item<R>(P, k + h * st, valid(k), acc, cmp, sl, lg);
         if (!ha) break;
         k += G * st;
     }
@@ -395,6 +402,7 @@ __device__ __forceinline__ void enter_group(const KParams &P, int g, R *sm, int 
     V.part = G.part;
     V.sb = G.s_bits;
     V.pb = G.pp_bits;
+    V.lg = G.lanes_log2;
     V.Nglob = reinterpret_cast<const R *>(P.popN) + G.N_inst;
     const R *src0 = reinterpret_cast<const R *>(G.part == PART_PP ? P.popP : P.popf) + G.stage0_src;
     const R *src1 = reinterpret_cast<const R *>(P.popN) + G.stage1_src;
@@ -422,7 +430,7 @@ __device__ __forceinline__ void enter_group(const KParams &P, int g, R *sm, int 
 // counter until none is left, so that SMs that finish early absorb the tail of the work.
 // Items are round-robin over the warps of the CTA; every item writes its own partial, so the
 // result does not depend on which CTA ran it.
-template <class R, bool STAGED, bool PIPE, int MINB>
+template <class R, bool STAGED, bool PIPE, bool WIDE, int MINB>
 __global__ void __launch_bounds__(kRhsThreads, MINB) rhs_kernel(KParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_chunk;
@@ -468,7 +476,7 @@ __global__ void __launch_bounds__(kRhsThreads, MINB) rhs_kernel(KParams P) {
         if (P.ctl && P.ctl[G.inst].done) continue;  // instance already at its t_out
         GroupView<R> V;
         enter_group<R, STAGED>(P, ug, sm, staged, V);
-        run_range<R, PIPE, kItemLanes>(P, V, ua + warp, ub, nwarps, lane);
+        run_range<R, PIPE, WIDE>(P, V, ua + warp, ub, nwarps, lane);
     }
     if (dynamic && P.n_tail > 0 && threadIdx.x == 0) {  // the last CTA out resets the counters
         __threadfence();
@@ -655,7 +663,19 @@ int make_plan(rtbte_ctx *ctx) {
     std::vector<Group> groups;
     std::vector<int> eoff, poff, ppoff;
     std::vector<InstDev> idev(ctx->inst.size());
-    const int cut = 16 * kItemLanes;  // entries per item at most
+    int cut = 512;  // entries per item at most (16 << the current group's lanes_log2)
+    // lanes per item of a group: from the mean (padded) length of its non-empty segments
+    // [s0, s1) of a CSR offset array, so that a sub-warp's item holds about one segment
+    auto lanes_log2 = [](const std::vector<long long> &off, long long s0, long long s1) {
+        long long tot = 0, n = 0;
+        for (long long s = s0; s < s1; ++s)
+            if (off[s + 1] > off[s]) {
+                tot += off[s + 1] - off[s];
+                ++n;
+            }
+        const double mean = n ? (double)tot / (double)n : 0.0;
+        return mean <= 128.0 ? 3 : mean <= 256.0 ? 4 : 5;
+    };
     auto add_seg = [&](long long b, long long e, int dest, int proc) {
         for (long long x = b; x < e; x += cut) {
             Item it;
@@ -686,6 +706,8 @@ int make_plan(rtbte_ctx *ctx) {
             G.stage0_src = I.f_off;
             G.stage1_len = I.N_q_pad;
             G.stage1_src = I.N_off + (long long)nu * I.N_q_pad;
+            G.lanes_log2 = lanes_log2(I.eph_off, 2LL * nu * I.d.n_c, 2LL * (nu + 1) * I.d.n_c);
+            cut = 16 << G.lanes_log2;
             G.f_inst = I.f_off;
             G.N_inst = I.N_off;
             G.P_inst = I.P_off;
@@ -718,6 +740,8 @@ int make_plan(rtbte_ctx *ctx) {
         G.n_q_pad = I.N_q_pad;
         G.stage0_len = I.n_c_pad;
         G.stage0_src = I.f_off;
+        G.lanes_log2 = lanes_log2(I.phe_off, 0, I.n_ph);
+        cut = 16 << G.lanes_log2;
         G.f_inst = I.f_off;
         G.N_inst = I.N_off;
         G.P_inst = I.P_off;
@@ -749,6 +773,8 @@ int make_plan(rtbte_ctx *ctx) {
         G.pp_bits = I.pp_bits;
         G.stage0_len = I.M_pad;
         G.stage0_src = I.P_off;
+        G.lanes_log2 = lanes_log2(I.pp_off, 0, 2 * I.M);
+        cut = 16 << G.lanes_log2;
         G.f_inst = I.f_off;
         G.N_inst = I.N_off;
         G.P_inst = I.P_off;
@@ -768,6 +794,7 @@ int make_plan(rtbte_ctx *ctx) {
     if (items.size() >= (size_t)INT32_MAX) return fail(ctx, RTBTE_E_UNSUPPORTED, "too many work items");
     ctx->n_items = (int)items.size();
     ctx->n_groups = (int)groups.size();
+    ctx->wide = std::all_of(groups.begin(), groups.end(), [](const Group &G) { return G.lanes_log2 == 5; });
     // instance layout for the row kernels
     std::vector<int> compact;
     for (size_t i = 0; i < ctx->inst.size(); ++i) {
@@ -794,10 +821,16 @@ int make_plan(rtbte_ctx *ctx) {
     int per_sm = 1;
     ctx->threads = kRhsThreads;
     if (ctx->staged) {
-        const void *kfn = ctx->precision == RTBTE_PREC_FP64 ? (const void *)rhs_kernel<double, true, false, 1>
-                                                             : (const void *)rhs_kernel<float, true, true, 1>;
-        RT_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_bytes));
-        RT_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        const bool fp64 = ctx->precision == RTBTE_PREC_FP64;
+        const void *kfns[2] = {fp64 ? (const void *)rhs_kernel<double, true, false, true, 1>
+                                    : (const void *)rhs_kernel<float, true, true, true, 1>,
+                               fp64 ? (const void *)rhs_kernel<double, true, false, false, 1>
+                                    : (const void *)rhs_kernel<float, true, true, false, 1>};
+        for (const void *f : kfns) {
+            RT_CUDA(ctx, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_bytes));
+            RT_CUDA(ctx, cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        }
+        const void *kfn = kfns[ctx->wide ? 0 : 1];
         for (int k : {4, 2}) {
             int nb = 0;
             RT_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, kRhsThreads / k, ctx->smem_bytes));
@@ -898,9 +931,12 @@ static int launch_core_t(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStr
         }
     }
     if (ctx->staged) {
-        rhs_kernel<R, true, sizeof(R) == 4, 1><<<ctx->grid, ctx->threads, ctx->smem_bytes, s>>>(P);
+        if (ctx->wide)
+            rhs_kernel<R, true, sizeof(R) == 4, true, 1><<<ctx->grid, ctx->threads, ctx->smem_bytes, s>>>(P);
+        else
+            rhs_kernel<R, true, sizeof(R) == 4, false, 1><<<ctx->grid, ctx->threads, ctx->smem_bytes, s>>>(P);
     } else {
-        rhs_kernel<R, false, false, 2><<<ctx->grid, ctx->threads, 0, s>>>(P);
+        rhs_kernel<R, false, false, false, 2><<<ctx->grid, ctx->threads, 0, s>>>(P);
     }
     RT_CUDA(ctx, cudaGetLastError());
     ctx->launches++;

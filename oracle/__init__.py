@@ -79,10 +79,22 @@ class OrErkOpts(C.Structure):
 class OrStats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("attempts", C.c_int64), ("fails", C.c_int64), ("rhs_evals", C.c_int64),
                 ("rhs_slow", C.c_int64), ("slow_steps", C.c_int64), ("t", C.c_double), ("h_last", C.c_double),
-                ("h_next", C.c_double), ("status", C.c_int)]
+                ("h_next", C.c_double), ("status", C.c_int), ("slow_fails", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class OrSlowOpts(C.Structure):
+    _fields_ = [("hs0", C.c_double), ("safety", C.c_double), ("fac_min", C.c_double), ("fac_max", C.c_double),
+                ("fast_scale", C.c_double), ("max_fail", C.c_int)]
+
+
+def slow_opts(hs0, safety=0.9, fac_min=0.2, fac_max=5.0, fast_scale=0.1, max_fail=7):
+    """Slow-step control of the tolerance-chosen MRI (library constants; not in the paper)."""
+    o = OrSlowOpts()
+    o.hs0, o.safety, o.fac_min, o.fac_max, o.fast_scale, o.max_fail = hs0, safety, fac_min, fac_max, fast_scale, max_fail
+    return o
 
 
 RHS_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double))
@@ -117,6 +129,7 @@ def lib():
             L.or_erk_solve.argtypes = [vp, vp, C.c_long, dbl, dbl, vp, vp, vp, vp]
             L.or_rk4_solve.argtypes = [vp, vp, C.c_long, dbl, dbl, dbl, vp, vp]
             L.or_mri_solve.argtypes = [vp, vp, vp, vp, C.c_long, dbl, dbl, dbl, vp, vp, vp]
+            L.or_mri_adapt_solve.argtypes = [vp, vp, vp, vp, C.c_long, dbl, dbl, vp, vp, vp, vp]
             L.or_split_rk4_solve.argtypes = [vp, vp, vp, vp, C.c_long, dbl, dbl, dbl, dbl, vp, vp]
             L.or_mis_coef.argtypes = [i32, vp, vp]
             L.or_num_threads.restype = i32
@@ -310,6 +323,21 @@ class Oracle:
                            C.addressof(o), C.addressof(st))
         return y, st.as_dict()
 
+    def mri_adapt(self, y0, t0, t1, hs0, rtol=1e-5, atol_c=1e-9, atol_ph=1e-12, slow=None, **kw):
+        """MRI with the slow step chosen from (rtol, atol) by step doubling; `slow`: dict of
+        slow_opts keywords other than hs0."""
+        Pf = self.problem(FAST)
+        Ps = self.problem(SLOW)
+        y = np.array(y0, np.float64, copy=True)
+        atol = self.atol_vec(atol_c, atol_ph)
+        o = erk_opts(kw.pop("method", ZON43), rtol, atol, **kw)
+        so = slow_opts(hs0, **(slow or {}))
+        st = OrStats()
+        fn = self._fn()
+        lib().or_mri_adapt_solve(fn, C.addressof(Pf), fn, C.addressof(Ps), y.shape[0], t0, t1, C.addressof(so),
+                                 _p(y), C.addressof(o), C.addressof(st))
+        return y, st.as_dict()
+
     def split_rk4(self, y0, t0, t1, hs, hf):
         Pf = self.problem(FAST)
         Ps = self.problem(SLOW)
@@ -376,6 +404,18 @@ def ode_mri(ff, fs, y0, t0, t1, hs, rtol, atol, **kw):
     st = OrStats()
     lib().or_mri_solve(C.cast(cf, C.c_void_p), None, C.cast(cs, C.c_void_p), None, n, t0, t1, hs, _p(y),
                        C.addressof(o), C.addressof(st))
+    return y, st.as_dict()
+
+
+def ode_mri_adapt(ff, fs, y0, t0, t1, hs0, rtol, atol, slow=None, **kw):
+    y = np.array(y0, np.float64, copy=True)
+    n = y.shape[0]
+    cf, cs = _wrap_py(ff, n), _wrap_py(fs, n)
+    o = erk_opts(kw.pop("method", ZON43), rtol, np.broadcast_to(np.asarray(atol, np.float64), (n,)).copy(), **kw)
+    so = slow_opts(hs0, **(slow or {}))
+    st = OrStats()
+    lib().or_mri_adapt_solve(C.cast(cf, C.c_void_p), None, C.cast(cs, C.c_void_p), None, n, t0, t1,
+                             C.addressof(so), _p(y), C.addressof(o), C.addressof(st))
     return y, st.as_dict()
 
 

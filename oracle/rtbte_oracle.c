@@ -747,6 +747,7 @@ typedef struct {
     int64_t steps, attempts, fails, rhs_evals, rhs_slow, slow_steps;
     double t, h_last, h_next;
     int status;
+    int64_t slow_fails; /* rejected slow steps (tolerance-chosen slow step) */
 } or_stats;
 
 enum { OR_OK = 0, OR_TOO_MANY_STEPS = -4, OR_STEP_UNDERFLOW = -5, OR_ERR_TEST_FAIL = -6, OR_NONFINITE = -7 };
@@ -935,52 +936,154 @@ static void forced_rhs(void *user, double t, const double *y, double *ydot) {
     for (long i = 0; i < F->n; ++i) ydot[i] += F->r[i];
 }
 
-/* Explicit MRI step sequence (Methods B, algorithm steps 1-3) with MIS coupling on
- * the Knoth-Wolke base: fixed slow step hs, fast auxiliary ODEs solved by the
- * adaptive ERK of `inner`.  Each fast solve restarts the error history; its first
- * step is the previous fast solve's proposal (estimated on the very first solve). */
-int or_mri_solve(or_rhs_fn ff, void *fu, or_rhs_fn fs, void *su, long n, double t0, double t1, double hs, double *y,
-                 const or_erk_opts *inner, or_stats *st) {
+/* One explicit MRI slow step (Methods B, algorithm steps 1-3) with MIS coupling on the
+ * Knoth-Wolke base, from t over H: slow RHS at each stage start, constant forcing
+ * r_i = (1/dc_i) sum_{j<i} Om_ij fs_j on the stage's sub-interval, fast auxiliary ODE solved by
+ * the adaptive ERK of `inner`, which restarts its error history per stage and starts from the
+ * carried proposal *h_in (0: estimate), clipped to the sub-interval.  Fs holds S + 1 vectors. */
+static int mis_step(or_rhs_fn ff, void *fu, or_rhs_fn fs, void *su, long n, double t, double H, double *y,
+                    const or_erk_opts *inner, double *h_in, double *Fs, or_stats *st) {
     double Om[36], chat[6];
     or_mis_coef(OR_KW3, Om, chat);
-    int S = 3;
-    double *Fs = (double *)malloc(sizeof(double) * (size_t)n * (S + 1));
+    const int S = 3;
     double *r = Fs + (size_t)n * S;
+    or_forced F = {ff, fu, r, n};
+    int status = OR_OK;
+    fs(su, t, y, Fs); /* stage 1: z_1 = y */
+    st->rhs_slow++;
+    for (int i = 1; i <= S; ++i) {
+        double dc = chat[i] - chat[i - 1];
+        double ta = t + chat[i - 1] * H, tb = (i == S) ? t + H : t + chat[i] * H;
+        for (long q = 0; q < n; ++q) {
+            double acc = 0.0;
+            for (int j = 0; j < i; ++j) acc += Om[i * 6 + j] * Fs[(size_t)j * n + q];
+            r[q] = acc / dc;
+        }
+        if (*h_in > tb - ta) *h_in = tb - ta;
+        or_stats in = {0};
+        status = or_erk_solve(forced_rhs, &F, n, ta, tb, y, inner, h_in, &in);
+        st->steps += in.steps;
+        st->attempts += in.attempts;
+        st->fails += in.fails;
+        st->rhs_evals += in.rhs_evals;
+        if (status != OR_OK) break;
+        if (i < S) {
+            fs(su, tb, y, Fs + (size_t)i * n);
+            st->rhs_slow++;
+        }
+    }
+    return status;
+}
+
+/* Explicit MRI with a fixed slow step hs (the last step ends at t1).  Each fast solve
+ * restarts the error history; its first step is the previous fast solve's proposal
+ * (estimated on the very first solve). */
+int or_mri_solve(or_rhs_fn ff, void *fu, or_rhs_fn fs, void *su, long n, double t0, double t1, double hs, double *y,
+                 const or_erk_opts *inner, or_stats *st) {
+    double *Fs = (double *)malloc(sizeof(double) * (size_t)n * 4);
     double t = t0;
     double h_in = 0.0;
     int status = OR_OK;
-    or_forced F = {ff, fu, r, n};
     long nsteps = (long)ceil((t1 - t0) / hs - 1e-9);
     for (long k = 0; k < nsteps && status == OR_OK; ++k) {
         double H = (k == nsteps - 1) ? t1 - t : hs;
-        /* stage 1: z_1 = y */
-        fs(su, t, y, Fs);
-        st->rhs_slow++;
-        for (int i = 1; i <= S; ++i) {
-            double dc = chat[i] - chat[i - 1];
-            double ta = t + chat[i - 1] * H, tb = (i == S) ? t + H : t + chat[i] * H;
-            for (long q = 0; q < n; ++q) {
-                double acc = 0.0;
-                for (int j = 0; j < i; ++j) acc += Om[i * 6 + j] * Fs[(size_t)j * n + q];
-                r[q] = acc / dc;
-            }
-            if (h_in > tb - ta) h_in = tb - ta;
-            or_stats in = {0};
-            status = or_erk_solve(forced_rhs, &F, n, ta, tb, y, inner, &h_in, &in);
-            st->steps += in.steps;
-            st->attempts += in.attempts;
-            st->fails += in.fails;
-            st->rhs_evals += in.rhs_evals;
-            if (status != OR_OK) break;
-            if (i < S) {
-                fs(su, tb, y, Fs + (size_t)i * n);
-                st->rhs_slow++;
-            }
-        }
+        status = mis_step(ff, fu, fs, su, n, t, H, y, inner, &h_in, Fs, st);
         t = (k == nsteps - 1) ? t1 : t + H;
         st->slow_steps++;
     }
     st->t = t;
+    st->status = status;
+    free(Fs);
+    return status;
+}
+
+/* Slow-step control of the tolerance-chosen MRI (the method's stated extension: h_s chosen
+ * from a tolerance instead of fixed).  Not in the paper; constants are library choices. */
+typedef struct {
+    double hs0;        /* first slow step                                              */
+    double safety;     /* step factor safety (0.9)                                     */
+    double fac_min;    /* smallest step factor (0.2)                                   */
+    double fac_max;    /* largest step factor after an accepted step (5)               */
+    double fast_scale; /* the fast ERK runs at rtol and atol times this (0.1)          */
+    int max_fail;      /* consecutive rejected slow steps before giving up (7)         */
+} or_slow_opts;
+
+/* MRI (MIS on Knoth-Wolke, order 3) with the slow step chosen from the tolerance by step
+ * doubling (Richardson extrapolation; Hairer, Norsett & Wanner, Solving ODEs I, Sec. II.4):
+ * from the state y_n at t, one slow step of H gives y_1 and two of H/2 give y_2; the local
+ * error of y_2 is estimated as (y_1 - y_2) / (2^3 - 1) and measured by the WRMS norm of
+ * `inner`'s rtol / atol with weights from y_n (Eq. wrms_norm, Eq. wrms_weights).  eps <= 1
+ * accepts y_2 and t + H; otherwise y_n is restored.  Next H = H * min(fac_max, max(fac_min,
+ * safety * eps^(-1/4))), the factor capped at 1 after a rejection and on the attempt that
+ * follows one.  The fast solves use rtol and atol scaled by fast_scale, so that their errors
+ * stay below the slow estimate.  Both the single step and the first half step start from the
+ * fast proposal held at y_n; an accepted step continues from the second half step's. */
+int or_mri_adapt_solve(or_rhs_fn ff, void *fu, or_rhs_fn fs, void *su, long n, double t0, double t1,
+                       const or_slow_opts *so, double *y, const or_erk_opts *inner, or_stats *st) {
+    double *Fs = (double *)malloc(sizeof(double) * (size_t)n * 8);
+    double *y0 = Fs + (size_t)n * 4, *y1 = y0 + n, *err = y1 + n, *atol_in = err + n;
+    or_erk_opts in = *inner;
+    in.rtol = inner->rtol * so->fast_scale;
+    for (long i = 0; i < n; ++i) atol_in[i] = inner->atol[i] * so->fast_scale;
+    in.atol = atol_in;
+    double t = t0, H = so->hs0, h_in = 0.0;
+    int status = OR_OK, nfail = 0, after_fail = 0;
+    while (t < t1 && status == OR_OK) {
+        if (inner->max_steps > 0 && st->slow_steps >= inner->max_steps) { status = OR_TOO_MANY_STEPS; break; }
+        double Hk = H;
+        int last = 0;
+        if (t + Hk >= t1) { Hk = t1 - t; last = 1; }
+        memcpy(y0, y, sizeof(double) * (size_t)n);
+        const double h0 = h_in;
+        /* one step of Hk */
+        memcpy(y1, y0, sizeof(double) * (size_t)n);
+        double hb = h0;
+        status = mis_step(ff, fu, fs, su, n, t, Hk, y1, &in, &hb, Fs, st);
+        if (status != OR_OK) break; /* y still holds y_n */
+        /* two steps of Hk / 2 */
+        const double Hh = 0.5 * Hk, tm = t + Hh;
+        double hh = h0;
+        status = mis_step(ff, fu, fs, su, n, t, Hh, y, &in, &hh, Fs, st);
+        if (status == OR_OK) status = mis_step(ff, fu, fs, su, n, tm, Hh, y, &in, &hh, Fs, st);
+        if (status != OR_OK) { /* hand back the last accepted state */
+            memcpy(y, y0, sizeof(double) * (size_t)n);
+            break;
+        }
+        int finite = 1;
+        for (long i = 0; i < n; ++i) {
+            err[i] = (y1[i] - y[i]) / 7.0; /* error of y_2: (y_1 - y_2) / (2^3 - 1) */
+            if (!isfinite(y[i])) finite = 0;
+        }
+        double eps = or_wrms(n, err, y0, inner->rtol, inner->atol);
+        if (!finite || !isfinite(eps)) { status = OR_NONFINITE; break; }
+        if (eps <= 1.0) {
+            t = last ? t1 : t + Hk;
+            h_in = hh;
+            st->slow_steps++;
+            st->h_last = Hk;
+            double e = eps > 1e-10 ? eps : 1e-10;
+            double fac = so->safety * pow(e, -0.25);
+            double cap = after_fail ? 1.0 : so->fac_max;
+            if (fac > cap) fac = cap;
+            if (fac < so->fac_min) fac = so->fac_min;
+            H = Hk * fac;
+            nfail = 0;
+            after_fail = 0;
+        } else {
+            memcpy(y, y0, sizeof(double) * (size_t)n);
+            h_in = h0;
+            st->slow_fails++;
+            if (++nfail >= so->max_fail) { status = OR_ERR_TEST_FAIL; break; }
+            double fac = so->safety * pow(eps, -0.25);
+            if (fac > 1.0) fac = 1.0;
+            if (fac < so->fac_min) fac = so->fac_min;
+            H = Hk * fac;
+            after_fail = 1;
+        }
+        if (t < t1 && !(t + H > t)) { status = OR_STEP_UNDERFLOW; break; }
+    }
+    st->t = t;
+    st->h_next = H;
     st->status = status;
     free(Fs);
     return status;

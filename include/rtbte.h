@@ -149,13 +149,17 @@ typedef struct rtbte_sizes {
 #define RTBTE_ZON43 2     /* adaptive Zonneveld 4(3) (ARKODE's default ERK)               */
 #define RTBTE_MRI_KW3 3   /* MIS on Knoth-Wolke, fixed slow step h_s, adaptive fast ERK  */
 #define RTBTE_SPLIT_RK4 4 /* first-order splitting: RK4 slow step h_s, RK4 fast steps h  */
+#define RTBTE_MRI_ADAPT 5 /* MIS on Knoth-Wolke with the slow step chosen from rtol/atol by
+                             step doubling (the extension the Discussion names as future
+                             work: slow and fast steps both from tolerances), adaptive fast
+                             ERK; the learned slow stage is not used by this method      */
 
 typedef struct rtbte_integ {
-    int32_t method;        /* RTBTE_RK4 .. RTBTE_SPLIT_RK4                                */
+    int32_t method;        /* RTBTE_RK4 .. RTBTE_MRI_ADAPT                                */
     int32_t fast_method;   /* inner ERK of MRI: RTBTE_ZON43 (default) or RTBTE_BS32      */
     double t0;             /* time of the incoming state y                                */
     double h;              /* RK4 step; SPLIT_RK4 fast step                               */
-    double h_s;            /* MRI / SPLIT_RK4 slow step                                   */
+    double h_s;            /* MRI / SPLIT_RK4 slow step; MRI_ADAPT: first slow step       */
     double rtol, atol_c, atol_ph;   /* Eq. wrms_weights; atol per carrier / phonon row   */
     double h0;             /* first step (<= 0: Hairer-Norsett-Wanner estimate)           */
     double hmin, hmax;     /* 0: unbounded                                                */
@@ -167,8 +171,21 @@ typedef struct rtbte_integ {
     int32_t small_nef;     /* failures before etamxf applies (default 2)                  */
     int32_t chunk;         /* attempts per launch of the device attempt loop (0: 64)      */
     int32_t resume;        /* 1: continue the controller of the previous call (step proposal,
-                              error history; no first-step estimate) -- see rtbte_controller */
+                              error history; no first-step estimate; MRI_ADAPT: also the slow
+                              step proposal) -- see rtbte_controller                          */
     int32_t reserved2;
+    /* MRI_ADAPT only (not in the paper; 0 selects the library default in brackets).  Each slow
+     * attempt from y_n takes one MIS step of H (y_1) and two of H/2 (y_2); the local error of
+     * y_2 is (y_1 - y_2) / (2^3 - 1), its WRMS norm eps uses rtol, atol_c, atol_ph and weights
+     * from y_n (Eq. wrms_norm, Eq. wrms_weights), the largest eps over instances decides:
+     * eps <= 1 accepts y_2, else y_n is restored.  Next H = H * min(fac_max, max(fac_min,
+     * safety * eps^(-1/4))), the factor at most 1 after a rejection and on the next attempt. */
+    double fast_tol_scale; /* fast ERK runs at rtol, atol_c, atol_ph times this [0.1]         */
+    double slow_safety;    /* [0.9]                                                           */
+    double slow_fac_min;   /* [0.2]                                                           */
+    double slow_fac_max;   /* [5]                                                             */
+    int32_t slow_max_fail; /* consecutive rejected slow steps before ERR_TEST_FAIL [7]        */
+    int32_t reserved3;
 } rtbte_integ;
 
 /* Step-size controller state of one instance (Eq. pid_controller), for checkpointing: save it
@@ -194,6 +211,8 @@ typedef struct rtbte_stats {
     double judge_err_max;                /* largest relative error seen by a judge (or -1)*/
     int64_t range_violations;            /* rows of accepted step states with f outside
                                             [-atol_c, 1+atol_c] or N < -atol_ph           */
+    int64_t slow_fails;                  /* MRI_ADAPT: rejected slow attempts             */
+    double h_slow_next;                  /* MRI_ADAPT: next slow step proposal            */
 } rtbte_stats;
 
 typedef struct rtbte_ctx rtbte_ctx;
@@ -243,7 +262,8 @@ int rtbte_phph_rates(rtbte_ctx *ctx, const double *y, double *rates);
  * the method of `opt`.  All stepping, error norms and step-size control run on the device:
  * each integration span is one launch of a CUDA graph whose WHILE node repeats the attempt
  * kernels until every instance is done (at most opt->chunk attempts per launch), and the host
- * reads the status block once per launch.  On success y holds the
+ * reads the status block once per launch (MRI_ADAPT: the host also reads the slow error
+ * norms once per slow attempt and decides it).  On success y holds the
  * solution at t_out; on failure y holds the last accepted state and st->t its time.
  * Synchronises the stream.  Errors: INVALID_ARG, STATE, TOO_MANY_STEPS, STEP_UNDERFLOW,
  * ERR_TEST_FAIL, NONFINITE, CUDA. */

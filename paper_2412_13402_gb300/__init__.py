@@ -29,7 +29,7 @@ RTBTE_EPH, RTBTE_PHE, RTBTE_PHPH = 1, 2, 4
 RTBTE_FAST, RTBTE_SLOW, RTBTE_ALL = 3, 4, 7
 RTBTE_PREC_FP32_COMP, RTBTE_PREC_FP64 = 0, 1
 RTBTE_CH_BUILD, RTBTE_CH_PREBUILT = 0, 1
-RTBTE_RK4, RTBTE_BS32, RTBTE_ZON43, RTBTE_MRI_KW3, RTBTE_SPLIT_RK4 = 0, 1, 2, 3, 4
+RTBTE_RK4, RTBTE_BS32, RTBTE_ZON43, RTBTE_MRI_KW3, RTBTE_SPLIT_RK4, RTBTE_MRI_ADAPT = 0, 1, 2, 3, 4, 5
 HBAR_EV_PS = 6.582119569e-4
 
 EXPORTS = ["rtbte_desc_defaults", "rtbte_integ_defaults", "rtbte_create", "rtbte_upload_channels", "rtbte_rhs",
@@ -75,7 +75,9 @@ class Integ(C.Structure):
                 ("a1", C.c_double), ("a2", C.c_double), ("a3", C.c_double), ("pid_sign_mode", C.c_int32),
                 ("max_nef", C.c_int32), ("safety", C.c_double), ("growth", C.c_double),
                 ("growth_first", C.c_double), ("etamxf", C.c_double), ("etamin", C.c_double),
-                ("small_nef", C.c_int32), ("chunk", C.c_int32), ("resume", C.c_int32), ("reserved2", C.c_int32)]
+                ("small_nef", C.c_int32), ("chunk", C.c_int32), ("resume", C.c_int32), ("reserved2", C.c_int32),
+                ("fast_tol_scale", C.c_double), ("slow_safety", C.c_double), ("slow_fac_min", C.c_double),
+                ("slow_fac_max", C.c_double), ("slow_max_fail", C.c_int32), ("reserved3", C.c_int32)]
 
 
 class Controller(C.Structure):
@@ -91,7 +93,8 @@ class Stats(C.Structure):
                 ("rhs_fast", C.c_int64), ("rhs_slow", C.c_int64), ("slow_steps", C.c_int64), ("t", C.c_double),
                 ("h_last", C.c_double), ("h_next", C.c_double), ("status", C.c_int32),
                 ("surrogate_fallbacks", C.c_int32), ("slow_exact", C.c_int64), ("slow_surrogate", C.c_int64),
-                ("judge_err_max", C.c_double), ("range_violations", C.c_int64)]
+                ("judge_err_max", C.c_double), ("range_violations", C.c_int64), ("slow_fails", C.c_int64),
+                ("h_slow_next", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -220,7 +223,7 @@ def instance_desc(model, keep: list) -> InstanceDesc:
 def integ_options(**kw) -> Integ:
     o = Integ()
     load().rtbte_integ_defaults(C.addressof(o))
-    names = {"method": {"rk4": 0, "bs32": 1, "zon43": 2, "mri": 3, "split_rk4": 4}}
+    names = {"method": {"rk4": 0, "bs32": 1, "zon43": 2, "mri": 3, "split_rk4": 4, "mri_adapt": 5}}
     for k, v in kw.items():
         if k in names and isinstance(v, str):
             v = names[k][v]

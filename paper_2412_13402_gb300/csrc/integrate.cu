@@ -21,6 +21,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "internal.cuh"
@@ -381,6 +382,39 @@ __global__ void mri_forcing(double *r, const double *Fs, double om0, double om1,
     }
 }
 
+// Tolerance-chosen MRI (step doubling on the MIS step): copy each instance's rows between its
+// current state buffer and buf (to_buf: current -> buf, else buf -> current).
+__global__ void copy_cur(RowParams Q, const Ctl *ctl, double *Y0, double *Y1, double *buf, long long n, int to_buf) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int ii = Q.n_inst > 1 ? find_inst(Q, c) : 0;
+        double *y = ctl[ii].cur ? Y1 : Y0;
+        if (to_buf) buf[c] = y[c]; else y[c] = buf[c];
+    }
+}
+
+// Squared weighted local-error estimate of the two-half-step result y_2 (the current state):
+// e = (y_1 - y_2) / (2^3 - 1) for the order-3 slow method, weights from y_n (Eq. wrms_weights).
+__global__ void __launch_bounds__(kRedThreads) slow_err_sq(RowParams Q, CtlParams cp, const Ctl *ctl, const double *Y0,
+                                                             const double *Y1, const double *yn, const double *y1,
+                                                             double *wsq, long long n) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int ii = Q.n_inst > 1 ? find_inst(Q, c) : 0;
+        const InstDev I = Q.inst[ii];
+        const double y2 = (ctl[ii].cur ? Y1 : Y0)[c];
+        const double w = 1.0 / (cp.rtol * fabs(yn[c]) + atol_of(cp, I, c - I.y_off));
+        const double d = (y1[c] - y2) / 7.0 * w;
+        wsq[c] = d * d;
+    }
+}
+
+// Per-instance WRMS norm (Eq. wrms_norm) from the chunk sums of wrms_chunks.
+__global__ void slow_eps(RowParams Q, const double *part, double *eps) {
+    const InstDev I = Q.inst[blockIdx.x];
+    const long long ni = (long long)I.n_c + I.n_ph;
+    const double sum = block_sum(part, (long long)blockIdx.x * kWrmsChunks, kWrmsChunks);
+    if (threadIdx.x == 0) eps[blockIdx.x] = sqrt(sum / (double)ni);
+}
+
 // ---- host helpers -----------------------------------------------------------------------
 int row_grid(rtbte_ctx *ctx) { return (int)std::min<long long>((ctx->n_y + kRedThreads - 1) / kRedThreads, kWrmsBlocks); }
 int n_inst(rtbte_ctx *ctx) { return (int)ctx->inst.size(); }
@@ -733,12 +767,15 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
     if (!st) st = &local;
     std::memset(st, 0, sizeof(*st));
     const int m = o->method;
-    if (m < RTBTE_RK4 || m > RTBTE_SPLIT_RK4) return fail(ctx, RTBTE_E_INVALID_ARG, "unknown method");
+    if (m < RTBTE_RK4 || m > RTBTE_MRI_ADAPT) return fail(ctx, RTBTE_E_INVALID_ARG, "unknown method");
     if (!(t_out > o->t0)) return fail(ctx, RTBTE_E_INVALID_ARG, "t_out must exceed t0");
     if ((m == RTBTE_RK4 || m == RTBTE_SPLIT_RK4) && !(o->h > 0)) return fail(ctx, RTBTE_E_INVALID_ARG, "h must be > 0");
-    if ((m == RTBTE_MRI_KW3 || m == RTBTE_SPLIT_RK4) && !(o->h_s > 0))
+    if ((m == RTBTE_MRI_KW3 || m == RTBTE_SPLIT_RK4 || m == RTBTE_MRI_ADAPT) && !(o->h_s > 0))
         return fail(ctx, RTBTE_E_INVALID_ARG, "h_s must be > 0");
-    if ((m == RTBTE_BS32 || m == RTBTE_ZON43 || m == RTBTE_MRI_KW3) &&
+    if (m == RTBTE_MRI_ADAPT && (o->fast_tol_scale < 0 || o->slow_safety < 0 || o->slow_fac_min < 0 ||
+                                 o->slow_fac_max < 0 || o->slow_max_fail < 0 || !(o->fast_tol_scale <= 1)))
+        return fail(ctx, RTBTE_E_INVALID_ARG, "slow-step options must be >= 0 (fast_tol_scale <= 1)");
+    if ((m == RTBTE_BS32 || m == RTBTE_ZON43 || m == RTBTE_MRI_KW3 || m == RTBTE_MRI_ADAPT) &&
         (!(o->rtol >= 0) || !(o->atol_c > 0) || !(o->atol_ph > 0)))
         return fail(ctx, RTBTE_E_INVALID_ARG, "tolerances must be positive");
     const size_t nb = sizeof(double) * ctx->n_y;
@@ -775,11 +812,19 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
         st->attempts = att;
         st->rhs_full = att * T.S + (est ? 2LL * NI : 0);
         gather_stats(ctx, st, false);
-    } else if (m == RTBTE_MRI_KW3) {
+    } else if (m == RTBTE_MRI_KW3 || m == RTBTE_MRI_ADAPT) {
+        const bool adapt = m == RTBTE_MRI_ADAPT;
         const Mis M = mis_kw3();
         const int fm = o->fast_method == RTBTE_BS32 ? RTBTE_BS32 : RTBTE_ZON43;
         const Tableau Tf = tableau_of(fm);
         CtlParams cp = ctl_params(o, Tf.p);
+        const CtlParams cps = cp;  // tolerances of the slow-step error norm (adaptive slow step)
+        if (adapt) {               // the fast solves run below the slow tolerance
+            const double fts = o->fast_tol_scale > 0 ? o->fast_tol_scale : 0.1;
+            cp.rtol *= fts;
+            cp.atol_c *= fts;
+            cp.atol_ph *= fts;
+        }
         if (!resume)
             for (int i = 0; i < NI; ++i) ctx->ctl_host[i].h = 0.0;
         if ((rc = write_ctl(ctx))) return rc;
@@ -797,7 +842,7 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
         a.respect_done = 0;
         // surrogate slow part (single instance): control variate about the last exact value,
         // exact judge every sur_period slow steps, exact for the rest of the call once a judge fails
-        bool sur_on = ctx->sur != nullptr && NI == 1;
+        bool sur_on = ctx->sur != nullptr && NI == 1 && !adapt;
         st->judge_err_max = -1.0;
         if (sur_on) {  // surrogate values write the sub-lattice rows only; the slow part is 0 elsewhere
             sur_reset(ctx);
@@ -813,24 +858,9 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
             return RTBTE_OK;
         };
         auto ycur = [&]() { return ctx->Y[ctx->ctl_host[0].cur].as<double>(); };
-        for (long long k = 0; k < nsteps && !failed; ++k) {
-            const double H = (k == nsteps - 1) ? t_out - t : o->h_s;
-            // slow RHS at z_1 = y
-            if (!sur_on || k % ctx->sur_period == 0) {
-                if ((rc = slow_exact(Fs))) return rc;
-                if (sur_on) {
-                    double e = 0;
-                    if ((rc = sur_judge(ctx, ycur(), Fs, &e))) return rc;
-                    st->judge_err_max = std::max(st->judge_err_max, e);
-                    if (e > ctx->sur_tol) {
-                        sur_on = false;
-                        st->surrogate_fallbacks = 1;
-                    }
-                }
-            } else {
-                if ((rc = sur_value(ctx, ycur(), Fs))) return rc;
-                st->slow_surrogate++;
-            }
+        // MIS stages 2..4 of one slow step from t over H (Fs holds the slow value at z_1 = y):
+        // constant forcing per stage, inner adaptive ERK over the stage's sub-interval
+        auto mis_stages = [&](double t, double H) -> int {
             for (int i = 1; i <= 3; ++i) {
                 const double dc = M.chat[i] - M.chat[i - 1];
                 const double ta = t + M.chat[i - 1] * H, tb = (i == 3) ? t + H : t + M.chat[i] * H;
@@ -858,14 +888,154 @@ int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rt
                     }
                 }
             }
-            if (failed) break;
-            t = (k == nsteps - 1) ? t_out : t + H;
-            st->slow_steps++;
+            return RTBTE_OK;
+        };
+        int slow_status = RTBTE_OK;
+        if (!adapt) {
+            for (long long k = 0; k < nsteps && !failed; ++k) {
+                const double H = (k == nsteps - 1) ? t_out - t : o->h_s;
+                // slow RHS at z_1 = y
+                if (!sur_on || k % ctx->sur_period == 0) {
+                    if ((rc = slow_exact(Fs))) return rc;
+                    if (sur_on) {
+                        double e = 0;
+                        if ((rc = sur_judge(ctx, ycur(), Fs, &e))) return rc;
+                        st->judge_err_max = std::max(st->judge_err_max, e);
+                        if (e > ctx->sur_tol) {
+                            sur_on = false;
+                            st->surrogate_fallbacks = 1;
+                        }
+                    }
+                } else {
+                    if ((rc = sur_value(ctx, ycur(), Fs))) return rc;
+                    st->slow_surrogate++;
+                }
+                if ((rc = mis_stages(t, H))) return rc;
+                if (failed) break;
+                t = (k == nsteps - 1) ? t_out : t + H;
+                st->slow_steps++;
+            }
+        } else {
+            // slow step from the tolerance by step doubling: one MIS step of Hk and two of Hk/2
+            // from y_n, local error of the latter (y_1 - y_2) / (2^3 - 1) in the WRMS norm of the
+            // slow tolerances with weights from y_n; the largest norm over instances decides
+            const double safety = o->slow_safety > 0 ? o->slow_safety : 0.9;
+            const double fac_min = o->slow_fac_min > 0 ? o->slow_fac_min : 0.2;
+            const double fac_max = o->slow_fac_max > 0 ? o->slow_fac_max : 5.0;
+            const int max_fail = o->slow_max_fail > 0 ? o->slow_max_fail : 7;
+            const size_t need = sizeof(double) * (2 * (size_t)n + (size_t)NI);
+            if (ctx->slow_save.bytes < need) {
+                ctx->slow_save.release();
+                RT_CUDA(ctx, cudaMalloc(&ctx->slow_save.p, need));
+                ctx->slow_save.bytes = need;
+            }
+            double *yn = ctx->slow_save.as<double>(), *y1 = yn + n, *eps_d = y1 + n;
+            double *Y0 = ctx->Y[0].as<double>(), *Y1 = ctx->Y[1].as<double>();
+            Ctl *cd = ctx->ctl.as<Ctl>();
+            const RowParams Q = row_params(ctx);
+            double *wsq = ctx->wrms_part.as<double>(), *part = wsq + 2 * n;
+            std::vector<double> h_in0(NI), eps_h(NI);
+            double H = resume && ctx->h_slow > 0 ? ctx->h_slow : o->h_s;
+            int nfail = 0;
+            bool after_fail = false;
+            auto copy = [&](double *buf, int to_buf) -> int {
+                copy_cur<<<nb2, kRedThreads, 0, ctx->stream>>>(Q, cd, Y0, Y1, buf, n, to_buf);
+                RT_CUDA(ctx, cudaGetLastError());
+                ctx->launches++;
+                return RTBTE_OK;
+            };
+            // back to y_n and the fast step proposals held there (the mirror is current: every
+            // fast solve ends with a controller read-back)
+            auto restore = [&](bool first0) -> int {
+                int r2;
+                if ((r2 = copy(yn, 0))) return r2;
+                for (int q = 0; q < NI; ++q) ctx->ctl_host[q].h = h_in0[q];
+                if ((r2 = write_ctl(ctx))) return r2;
+                first_inner = first0;
+                return RTBTE_OK;
+            };
+            while (t < t_out) {
+                if (st->slow_steps >= max_steps) {
+                    slow_status = RTBTE_E_TOO_MANY_STEPS;
+                    break;
+                }
+                double Hk = H;
+                bool last = false;
+                if (t + Hk >= t_out) {
+                    Hk = t_out - t;
+                    last = true;
+                }
+                if ((rc = copy(yn, 1))) return rc;
+                for (int q = 0; q < NI; ++q) h_in0[q] = ctx->ctl_host[q].h;
+                const bool first0 = first_inner;
+                // one step of Hk
+                if ((rc = slow_exact(Fs)) || (rc = mis_stages(t, Hk))) return rc;
+                if (failed) {
+                    if ((rc = restore(first0))) return rc;
+                    break;
+                }
+                if ((rc = copy(y1, 1)) || (rc = restore(first0))) return rc;
+                // two steps of Hk / 2
+                const double Hh = 0.5 * Hk, tm = t + Hh;
+                if ((rc = slow_exact(Fs)) || (rc = mis_stages(t, Hh))) return rc;
+                if (!failed && ((rc = slow_exact(Fs)) || (rc = mis_stages(tm, Hh)))) return rc;
+                if (failed) {
+                    if ((rc = restore(first0))) return rc;
+                    break;
+                }
+                slow_err_sq<<<nb2, kRedThreads, 0, ctx->stream>>>(Q, cps, cd, Y0, Y1, yn, y1, wsq, n);
+                wrms_chunks<<<dim3(kWrmsChunks, NI), kRedThreads, 0, ctx->stream>>>(Q, cd, wsq, part, 0);
+                slow_eps<<<NI, kRedThreads, 0, ctx->stream>>>(Q, part, eps_d);
+                RT_CUDA(ctx, cudaGetLastError());
+                ctx->launches += 3;
+                RT_CUDA(ctx, cudaMemcpyAsync(eps_h.data(), eps_d, sizeof(double) * NI, cudaMemcpyDeviceToHost,
+                                             ctx->stream));
+                RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+                double eps = 0.0;
+                bool finite = true;
+                for (double e : eps_h) {
+                    if (!std::isfinite(e)) finite = false;
+                    else eps = std::max(eps, e);
+                }
+                if (!finite) {
+                    slow_status = RTBTE_E_NONFINITE;
+                    if ((rc = restore(first0))) return rc;
+                    break;
+                }
+                if (eps <= 1.0) {  // accept y_2; the fast proposal continues from the second half step
+                    t = last ? t_out : t + Hk;
+                    st->slow_steps++;
+                    double fac = safety * std::pow(std::max(eps, 1e-10), -0.25);
+                    fac = std::min(fac, after_fail ? 1.0 : fac_max);
+                    fac = std::max(fac, fac_min);
+                    H = Hk * fac;
+                    nfail = 0;
+                    after_fail = false;
+                } else {
+                    if ((rc = restore(first0))) return rc;
+                    st->slow_fails++;
+                    if (++nfail >= max_fail) {
+                        slow_status = RTBTE_E_ERR_TEST_FAIL;
+                        break;
+                    }
+                    double fac = std::min(safety * std::pow(eps, -0.25), 1.0);
+                    fac = std::max(fac, fac_min);
+                    H = Hk * fac;
+                    after_fail = true;
+                }
+                if (t < t_out && !(t + H > t)) {
+                    slow_status = RTBTE_E_STEP_UNDERFLOW;
+                    break;
+                }
+            }
+            ctx->h_slow = H;
+            st->h_slow_next = H;
         }
         st->attempts = inner_attempts;
         st->rhs_fast = inner_attempts * Tf.S + 2LL * NI * inner_h0;
         gather_stats(ctx, st, false);
-        if (!failed) st->t = t;
+        if (!failed || adapt) st->t = t;
+        if (st->status == RTBTE_OK) st->status = slow_status;
     } else {  // first-order operator splitting with RK4 (slow step, then fast sub-steps)
         if ((rc = write_ctl(ctx))) return rc;
         long long nsteps = (long long)ceil((t_out - o->t0) / o->h_s - 1e-9);

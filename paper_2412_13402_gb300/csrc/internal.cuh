@@ -211,6 +211,8 @@ struct rtbte_ctx {
     // integrator work buffers
     rtbte::DevBuf Y[2], K, Fs, forcing, wrms_part, ctl, ystage, ydstage, range_scratch;  // wrms_part: 2 x n_y squared norms, then per-instance chunk sums
     rtbte::Ctl *ctl_host = nullptr;  // pinned mirror of the per-instance controllers
+    rtbte::DevBuf slow_save;          // tolerance-chosen MRI: y_n, the single-step result, error norms
+    double h_slow = 0.0;              // tolerance-chosen MRI: slow step proposal after the last call
     std::map<long long, cudaGraphExec_t> graphs;
     std::map<long long, int> graph_launches;  // kernels per attempt of each attempt-loop graph
     bool use_graphs = true;                   // attempts through the device-loop graph (else direct launches)

@@ -418,14 +418,18 @@ def silicon_study(rt, ri, dev, n=32, t_end=0.5):
     assert st_ref["status"] == 0, st_ref
     runs = []
     for prec in ("fp32", "fp64"):
-        for fam, kw in (("erk", dict(method="zon43", **tol)), ("mri", dict(method="mri", h_s=0.050, **tol))):
+        fams = [("erk", dict(method="zon43", **tol)), ("mri", dict(method="mri", h_s=0.050, **tol))]
+        if prec == "fp32":  # slow step from the tolerance (step doubling), fast solves at the same tolerance
+            fams += [("mri_adapt", dict(method="mri_adapt", h_s=0.050, fast_tol_scale=1.0, **{**tol, "rtol": r}))
+                     for r in (1e-5, 1e-6)]
+        for fam, kw in fams:
             y, st, sec = run(ctxs[prec], **kw)
-            runs.append({"precision": prec, "method": fam, "status": st["status"], "seconds": sec,
+            runs.append({"precision": prec, "method": fam, "rtol": kw["rtol"], "status": st["status"], "seconds": sec,
                          "sim_ps_per_s": t_end / sec,
                          "err_carriers": float(np.linalg.norm(y[:nc] - ref[:nc]) / np.linalg.norm(ref[:nc])),
                          "err_phonons": float(np.linalg.norm(y[nc:] - ref[nc:]) / np.linalg.norm(ref[nc:])),
                          "steps": st["steps"], "rhs_full": st["rhs_full"], "rhs_fast": st["rhs_fast"],
-                         "rhs_slow": st["rhs_slow"]})
+                         "rhs_slow": st["rhs_slow"], "slow_steps": st["slow_steps"], "slow_fails": st["slow_fails"]})
     for c in ctxs.values():
         c.close()
     out["reference"] = {"method": "zon43", "precision": "fp64", "rtol": 1e-9, "seconds": t_ref, "steps": st_ref["steps"]}

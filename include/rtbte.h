@@ -109,7 +109,13 @@ typedef struct rtbte_desc {
     double hbar;          /* eV*ps                                                   */
     void *stream;         /* cudaStream_t used for every launch (NULL: default stream) */
     int32_t device;       /* CUDA device ordinal (must be current for every call)    */
-    int32_t reserved1;
+    int32_t eph_q_blocks; /* built e-ph lists of each mode split by phonon wavevector into
+                             this many contiguous q-blocks, so that the populations a block
+                             reads (f and that block of the mode's N) fit in shared memory:
+                             0 = automatic (1 when f and the whole mode's N fit, else the
+                             fewest equal blocks that fit); prebuilt lists always use 1.
+                             Segment order of built e-ph lists: (mode, block, electron,
+                             process), sources ascending within a segment               */
 } rtbte_desc;
 
 /* Channel source for rtbte_upload_channels.
@@ -141,6 +147,8 @@ typedef struct rtbte_sizes {
     int64_t eph_stored, phe_stored, pp_stored;           /* stored, incl. padding    */
     int64_t work_items;                                  /* whole context            */
     int64_t channel_bytes;                               /* device bytes, this inst. */
+    int64_t eph_q_blocks;                                /* q-blocks per mode of the stored
+                                                            e-ph lists (rtbte_desc)    */
 } rtbte_sizes;
 
 /* ---- integrators (Methods B) --------------------------------------------- */
@@ -273,9 +281,11 @@ int rtbte_advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ 
 int rtbte_get_sizes(const rtbte_ctx *ctx, int inst, rtbte_sizes *out);
 
 /* Copy instance `inst`'s stored lists back to host in the PREBUILT logical order (padding
- * removed).  which: RTBTE_EPH, RTBTE_PHE or RTBTE_PHPH.  off must hold the segment count
- * + 1 entries; a/b/W must hold the logical entry count (rtbte_get_sizes).  For e-ph a/b
- * are (src, phonon); ph-e (dst, src); ph-ph (b, c).  Synchronous. */
+ * removed; q-blocked e-ph lists are merged back into segments (mode, electron, process) with
+ * sources ascending).  which: RTBTE_EPH, RTBTE_PHE or RTBTE_PHPH.  off must hold the segment
+ * count + 1 entries (e-ph 2*nmodes*n_c, ph-e n_ph, ph-ph 2*n_pp); a/b/W must hold the logical
+ * entry count (rtbte_get_sizes).  For e-ph a/b are (src, phonon); ph-e (dst, src); ph-ph
+ * (b, c).  Synchronous. */
 int rtbte_download_channels(rtbte_ctx *ctx, int inst, unsigned which, int64_t *off, int32_t *a, int32_t *b,
                             double *W);
 

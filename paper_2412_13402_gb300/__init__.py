@@ -53,7 +53,7 @@ class InstanceDesc(C.Structure):
 
 class Desc(C.Structure):
     _fields_ = [("n_instances", C.c_int32), ("precision", C.c_int32), ("inst", C.c_void_p), ("hbar", C.c_double),
-                ("stream", C.c_void_p), ("device", C.c_int32), ("reserved1", C.c_int32)]
+                ("stream", C.c_void_p), ("device", C.c_int32), ("eph_q_blocks", C.c_int32)]
 
 
 class Channels(C.Structure):
@@ -65,7 +65,7 @@ class Channels(C.Structure):
 class Sizes(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("n_c", "n_ph", "n_pp", "y_offset", "n_y_total", "eph_entries",
                                          "phe_entries", "pp_entries", "eph_stored", "phe_stored", "pp_stored",
-                                         "work_items", "channel_bytes")]
+                                         "work_items", "channel_bytes", "eph_q_blocks")]
 
 
 class Integ(C.Structure):
@@ -236,7 +236,8 @@ def integ_options(**kw) -> Integ:
 class Context:
     """One library context over one or more independent instances sharing a state vector."""
 
-    def __init__(self, models, precision: str = "fp32", stream=None, device: int = 0, hbar: float = HBAR_EV_PS):
+    def __init__(self, models, precision: str = "fp32", stream=None, device: int = 0, hbar: float = HBAR_EV_PS,
+                 eph_q_blocks: int = 0):
         import torch
 
         if not torch.cuda.is_available():
@@ -258,6 +259,7 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         d.stream = self.stream.cuda_stream
         d.device = device
+        d.eph_q_blocks = eph_q_blocks
         self.device = device
         self.ctx = rtbte_create(d)
 

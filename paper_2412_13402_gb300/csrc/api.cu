@@ -158,6 +158,8 @@ int upload_prebuilt(rtbte_ctx *ctx, InstHost &I, const rtbte_channels *ch) {
         return RTBTE_OK;
     };
     if (!ch->eph_off || !ch->phe_off) return fail(ctx, RTBTE_E_INVALID_ARG, "prebuilt e-ph and ph-e lists required");
+    I.eph_nqb = 1;  // prebuilt e-ph lists: segments (mode, electron, process)
+    I.eph_qblk = I.N_q_pad;
     int rc;
     rc = pack(2LL * nm * nc, ch->eph_off,
               [&](long long g, long long e, uint32_t *code) {
@@ -220,11 +222,38 @@ int download(rtbte_ctx *ctx, InstHost &I, unsigned which, int64_t *off, int32_t 
     const uint32_t smask = (1u << I.s_bits) - 1u, pmask = I.pp_bits ? (1u << I.pp_bits) - 1u : 0u;
     long long o = 0;
     off[0] = 0;
+    if (which == RTBTE_EPH && I.eph_nqb > 1) {
+        // q-blocked e-ph lists: merge each (mode, electron, process) segment's block sub-lists
+        // back into one list in ascending source order (a source occurs once per segment)
+        const long long nc = I.d.n_c, nqb = I.eph_nqb;
+        std::vector<std::pair<uint32_t, long long>> tmp;
+        for (long long nu = 0; nu < I.d.nmodes; ++nu)
+            for (long long d = 0; d < nc; ++d)
+                for (int proc = 0; proc < 2; ++proc) {
+                    tmp.clear();
+                    for (long long qb = 0; qb < nqb; ++qb) {
+                        const long long g = ((nu * nqb + qb) * nc + d) * 2 + proc;
+                        for (long long k = 0; k < (*cn)[g]; ++k) tmp.push_back({hidx[(*po)[g] + k], (*po)[g] + k});
+                    }
+                    std::sort(tmp.begin(), tmp.end(), [&](const std::pair<uint32_t, long long> &x,
+                                                          const std::pair<uint32_t, long long> &y) {
+                        return (x.first & smask) < (y.first & smask);
+                    });
+                    for (const auto &t : tmp) {
+                        a[o] = (int32_t)(t.first & smask);
+                        b[o] = (int32_t)(nu * I.N_q + (t.first >> I.s_bits));
+                        W[o] = (double)hW[t.second];
+                        ++o;
+                    }
+                    off[(nu * nc + d) * 2 + proc + 1] = o;
+                }
+        return RTBTE_OK;
+    }
     for (long long g = 0; g < nseg; ++g) {
         for (long long k = 0; k < (*cn)[g]; ++k) {
             const uint32_t e = hidx[(*po)[g] + k];
             if (which == RTBTE_EPH) {
-                const int nu = (int)(g / (2LL * I.d.n_c));
+                const int nu = (int)(g / (2LL * I.eph_nqb * I.d.n_c));
                 a[o] = (int32_t)(e & smask);
                 b[o] = (int32_t)((long long)nu * I.N_q + (e >> I.s_bits));
             } else if (which == RTBTE_PHE) {
@@ -286,7 +315,8 @@ void rtbte_integ_defaults(rtbte_integ *o) {
 
 int rtbte_create(const rtbte_desc *d, rtbte_ctx **out) {
     if (!d || !out || d->n_instances < 1 || !d->inst || !(d->hbar > 0) ||
-        (d->precision != RTBTE_PREC_FP32_COMP && d->precision != RTBTE_PREC_FP64))
+        (d->precision != RTBTE_PREC_FP32_COMP && d->precision != RTBTE_PREC_FP64) || d->eph_q_blocks < 0 ||
+        d->eph_q_blocks > 256)
         return RTBTE_E_INVALID_ARG;
     *out = nullptr;
     rtbte_ctx *ctx = new (std::nothrow) rtbte_ctx();
@@ -298,6 +328,7 @@ int rtbte_create(const rtbte_desc *d, rtbte_ctx **out) {
     };
     ctx->device = d->device;
     ctx->precision = d->precision;
+    ctx->eph_q_blocks = d->eph_q_blocks;
     ctx->real_size = d->precision == RTBTE_PREC_FP64 ? 8 : 4;
     ctx->hbar = d->hbar;
     ctx->stream = reinterpret_cast<cudaStream_t>(d->stream);
@@ -462,6 +493,7 @@ int rtbte_get_sizes(const rtbte_ctx *ctx, int inst, rtbte_sizes *out) {
     out->work_items = ctx->n_items;
     const long long es = 4 + (long long)ctx->real_size;
     out->channel_bytes = es * (out->eph_stored + out->phe_stored + out->pp_stored);
+    out->eph_q_blocks = I.has_channels ? I.eph_nqb : 0;
     return RTBTE_OK;
 }
 

@@ -113,16 +113,19 @@ __global__ void eph_enum(BuildTables T, long long *counts, const long long *off,
     const int d = (int)warp;
     const int4 kd = T.ek[d];
     const double ed = T.eps[d];
+    const unsigned lt = (1u << lane) - 1u;
+    // one scan of the sources per q-block: segments (mode, block, d, process), sources ascending
+    for (int qb = 0; qb < T.eph_nqb; ++qb) {
+    const int q_lo = qb * T.eph_qblk, q_hi = q_lo + T.eph_qblk;
     int run[2 * kMaxModes];
 #pragma unroll
     for (int i = 0; i < 2 * kMaxModes; ++i) run[i] = 0;
-    const unsigned lt = (1u << lane) - 1u;
     for (int base = 0; base < T.n_c; base += 32) {
         const int s = base + lane;
-        const bool valid = s < T.n_c;
-        int4 ks = valid ? T.ek[s] : kd;
-        double es = valid ? T.eps[s] : 0.0;
+        int4 ks = s < T.n_c ? T.ek[s] : kd;
+        double es = s < T.n_c ? T.eps[s] : 0.0;
         int q = q_index(T, kd, ks);
+        const bool valid = s < T.n_c && q >= q_lo && q < q_hi;
 #pragma unroll
         for (int nu = 0; nu < kMaxModes; ++nu) {
             if (nu >= T.nmodes) break;
@@ -134,7 +137,7 @@ __global__ void eph_enum(BuildTables T, long long *counts, const long long *off,
             bool kab = live && Dab <= T.cut_eph && Dab >= -T.cut_eph;
             unsigned bem = __ballot_sync(kFull, kem), bab = __ballot_sync(kFull, kab);
             if (FILL) {
-                long long seg = ((long long)nu * T.n_c + d) * 2;
+                long long seg = (((long long)nu * T.eph_nqb + qb) * T.n_c + d) * 2;
                 if (kem) {
                     long long at = off[seg] + run[2 * nu] + __popc(bem & lt);
                     idx[at] = (uint32_t)s | ((uint32_t)q << T.s_bits);
@@ -155,17 +158,19 @@ __global__ void eph_enum(BuildTables T, long long *counts, const long long *off,
         if (nu >= T.nmodes) break;
 #pragma unroll
         for (int proc = 0; proc < 2; ++proc) {
-            long long seg = ((long long)nu * T.n_c + d) * 2 + proc;
+            long long seg = (((long long)nu * T.eph_nqb + qb) * T.n_c + d) * 2 + proc;
             if (!FILL) {
                 if (lane == 0) counts[seg] = run[2 * nu + proc];
-            } else {  // zero-weight padding up to the next multiple of 4
+            } else {  // zero-weight padding up to the next multiple of 4; its phonon index is the
+                      // block's first q, so that its population read stays in the staged block
                 long long a0 = off[seg] + run[2 * nu + proc], a1 = off[seg + 1];
                 for (long long a = a0 + lane; a < a1; a += 32) {
-                    idx[a] = 0u;
+                    idx[a] = (uint32_t)q_lo << T.s_bits;
                     put_w<R>(W, a, 0.0);
                 }
             }
         }
+    }
     }
 }
 
@@ -370,6 +375,8 @@ BuildTables tables_of(rtbte_ctx *ctx, InstHost &I) {
     T.s_bits = I.s_bits;
     T.q_bits = I.q_bits;
     T.pp_bits = I.pp_bits;
+    T.eph_nqb = I.eph_nqb;
+    T.eph_qblk = I.eph_qblk;
     T.sigma_eph = I.d.sigma_eph;
     T.sigma_pp = I.d.sigma_pp;
     T.cut_eph = 3.0 * I.d.sigma_eph;
@@ -384,13 +391,34 @@ BuildTables tables_of(rtbte_ctx *ctx, InstHost &I) {
     return T;
 }
 
+// e-ph q-blocks of instance I: one when f and one mode's N fit in shared memory together (or
+// when f alone leaves under 16 KB, and the kernel reads populations from global memory anyway),
+// else the fewest equal blocks of whole multiples of 4 q points that fit; a count requested at
+// creation overrides the choice.
+void choose_q_blocks(rtbte_ctx *ctx, InstHost &I) {
+    const long long R = (long long)ctx->real_size;
+    const long long room = (long long)ctx->smem_optin - 64 - (long long)I.n_c_pad * R;
+    long long nqb = 1;
+    if (ctx->eph_q_blocks > 0)
+        nqb = ctx->eph_q_blocks;
+    else if ((long long)I.N_q_pad * R > room && room >= 16384)
+        nqb = ((long long)I.N_q_pad * R + room - 1) / room;
+    long long qblk = round_up((I.N_q + nqb - 1) / nqb, 4);
+    nqb = (I.N_q + qblk - 1) / qblk;
+    I.eph_nqb = (int)std::max<long long>(nqb, 1);
+    I.eph_qblk = (int)std::max<long long>(qblk, 4);
+}
+
 template <class R>
 int run_build(rtbte_ctx *ctx, InstHost &I) {
     BuildTables T = tables_of(ctx, I);
     const int threads = 256, wpb = threads / 32;
     DevBuf cnt, off;
-    // ---- e-ph
-    long long nseg = 2LL * I.d.nmodes * I.d.n_c;
+    // ---- e-ph, in q-blocks when f and a whole mode's N do not fit in shared memory together
+    choose_q_blocks(ctx, I);
+    T.eph_nqb = I.eph_nqb;
+    T.eph_qblk = I.eph_qblk;
+    long long nseg = 2LL * I.d.nmodes * I.eph_nqb * I.d.n_c;
     RT_CUDA(ctx, cudaMalloc(&cnt.p, sizeof(long long) * std::max<long long>(nseg, 1)));
     eph_enum<false, R><<<(unsigned)((I.d.n_c + wpb - 1) / wpb), threads, 0, ctx->stream>>>(T, cnt.as<long long>(),
                                                                                           nullptr, nullptr, nullptr);

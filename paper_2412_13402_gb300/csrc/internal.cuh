@@ -60,6 +60,7 @@ struct __align__(16) Group {
     int pp_bits, n_q_pad;
     int lanes_log2, pad_g;       // lanes per item = 1 << lanes_log2 (3, 4 or 5)
     int stage0_len, stage1_len;  // staged element counts (multiples of 4)
+    int stage1_q0, pad_s;        // e-ph: first q of the staged block of the mode's N
     long long stage0_src;        // popf (e-ph, ph-e) or popP (ph-ph) offset of the staged block
     long long stage1_src;        // popN offset of the staged mode slice (e-ph)
     long long f_inst, N_inst, P_inst;  // instance offsets in popf / popN / popP
@@ -69,7 +70,7 @@ struct __align__(16) Group {
 struct __align__(16) InstDev {
     long long y_off;
     int n_c, n_ph, M, nmodes;
-    int N_q, N_q_pad, pad0, pad1;
+    int N_q, N_q_pad, eblocks, pad1;  // eblocks: e-ph item-offset blocks (modes x q-blocks)
     long long f_off, N_off, P_off;  // offsets in popf / popN / popP
     long long eoff_base;            // item offsets of e-ph rows: [nmodes][n_c+1]
     long long poff_base;            // item offsets of ph-e rows: [n_ph+1]
@@ -149,6 +150,7 @@ struct BuildTables {
     int nk[3], nq[3], nqs[3];
     long long N_k, N_q, N_ph, M, N_qs;
     int s_bits, q_bits, pp_bits;
+    int eph_nqb, eph_qblk;  // e-ph q-blocks per mode, q points per block
     double cut_eph, cut_pp, sigma_eph, sigma_pp, omega_cut;
     double pref_eph, pref_phe, pref_pp;  // 2pi/(hbar N_q), 4pi/(hbar N_k), 36pi/(hbar N_q,pp)
     double v3;
@@ -163,6 +165,7 @@ struct InstHost {
     int nqs[3] = {1, 1, 1};
     int N_q_pad = 0, n_c_pad = 0, M_pad = 0;
     int s_bits = 0, q_bits = 0, pp_bits = 0;
+    int eph_nqb = 1, eph_qblk = 0;  // e-ph q-blocks per mode and their size in q points (multiple of 4)
     std::vector<int32_t> pp_full, pp_full_inv, compact;
     // builder tables (device), kept for rebuilds
     DevBuf t_ek, t_eps, t_eid, t_eidinv, t_omega, t_kmap, t_lut, t_g2, t_ppfull, t_ppinv;
@@ -213,6 +216,7 @@ struct rtbte_ctx {
     rtbte::Ctl *ctl_host = nullptr;  // pinned mirror of the per-instance controllers
     rtbte::DevBuf slow_save;          // tolerance-chosen MRI: y_n, the single-step result, error norms
     double h_slow = 0.0;              // tolerance-chosen MRI: slow step proposal after the last call
+    int eph_q_blocks = 0;             // requested e-ph q-blocks (0: automatic)
     std::map<long long, cudaGraphExec_t> graphs;
     std::map<long long, int> graph_launches;  // kernels per attempt of each attempt-loop graph
     bool use_graphs = true;                   // attempts through the device-loop graph (else direct launches)

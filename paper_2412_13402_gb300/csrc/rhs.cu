@@ -418,10 +418,10 @@ __device__ __forceinline__ void enter_group(const KParams &P, int g, R *sm, int 
             staged = g;
         }
         V.s0 = sm;
-        V.s1 = sm + l0;
+        V.s1 = sm + l0 - G.stage1_q0;  // indexed by the full q index of the mode
     } else {
         V.s0 = src0;
-        V.s1 = src1;
+        V.s1 = src1 - G.stage1_q0;
     }
 }
 
@@ -692,7 +692,11 @@ int make_plan(rtbte_ctx *ctx) {
     for (size_t i = 0; i < ctx->inst.size(); ++i) {
         InstHost &I = ctx->inst[i];
         idev[i].eoff_base = (long long)eoff.size();
-        for (int nu = 0; nu < I.d.nmodes; ++nu) {
+        const int nqb = std::max(I.eph_nqb, 1);
+        const int qblk = I.eph_qblk > 0 ? I.eph_qblk : I.N_q_pad;
+        for (int blk = 0; blk < I.d.nmodes * nqb; ++blk) {  // (mode, q-block)
+            const int nu = blk / nqb, qb = blk % nqb;
+            const int q_lo = qb * qblk, q_len = std::min(qblk, I.N_q_pad - q_lo);
             Group G{};
             G.idx = I.eph_idx.as<uint32_t>();
             G.W = I.eph_W.p;
@@ -704,16 +708,17 @@ int make_plan(rtbte_ctx *ctx) {
             G.n_q_pad = I.N_q_pad;
             G.stage0_len = I.n_c_pad;
             G.stage0_src = I.f_off;
-            G.stage1_len = I.N_q_pad;
-            G.stage1_src = I.N_off + (long long)nu * I.N_q_pad;
-            G.lanes_log2 = lanes_log2(I.eph_off, 2LL * nu * I.d.n_c, 2LL * (nu + 1) * I.d.n_c);
+            G.stage1_len = q_len;
+            G.stage1_src = I.N_off + (long long)nu * I.N_q_pad + q_lo;
+            G.stage1_q0 = q_lo;
+            G.lanes_log2 = lanes_log2(I.eph_off, 2LL * blk * I.d.n_c, 2LL * (blk + 1) * I.d.n_c);
             cut = 16 << G.lanes_log2;
             G.f_inst = I.f_off;
             G.N_inst = I.N_off;
             G.P_inst = I.P_off;
             for (int d = 0; d < I.d.n_c; ++d) {
                 eoff.push_back((int)items.size());
-                long long g = ((long long)nu * I.d.n_c + d) * 2;
+                long long g = ((long long)blk * I.d.n_c + d) * 2;
                 
                 add_seg(I.eph_off[g], I.eph_off[g + 1], d, 0);
                 add_seg(I.eph_off[g + 1], I.eph_off[g + 2], d, 1);
@@ -807,6 +812,7 @@ int make_plan(rtbte_ctx *ctx) {
         D.nmodes = I.d.nmodes;
         D.N_q = (int)I.N_q;
         D.N_q_pad = I.N_q_pad;
+        D.eblocks = I.d.nmodes * std::max(I.eph_nqb, 1);
         D.f_off = I.f_off;
         D.N_off = I.N_off;
         D.P_off = I.P_off;

@@ -61,8 +61,8 @@ __device__ __forceinline__ double row_value(const RowParams &Q, const InstDev &I
     if (local < I.n_c) {
         if (!(parts & RTBTE_EPH)) return 0.0;
         const int d = (int)local;
-        for (int nu = 0; nu < I.nmodes; ++nu) {
-            const int *o = Q.eoff + I.eoff_base + (long long)nu * (I.n_c + 1);
+        for (int blk = 0; blk < I.eblocks; ++blk) {  // (mode, q-block) blocks of item offsets
+            const int *o = Q.eoff + I.eoff_base + (long long)blk * (I.n_c + 1);
             item_sum<R>(Q, o[d], o[d + 1], A);
         }
         return -A.value();

@@ -370,12 +370,13 @@ SILICON_MODES = (("TA1", "ac", 0.020), ("TA2", "ac", 0.022), ("LA", "ac", 0.050)
 
 def silicon(n: int = 32, fold: int = 2, window: float = 0.4, seed: int = SEED_BASE + 2, T: float = 300.0,
             E_x: float = 0.2, amp: float = 0.2, width: float = 0.03, sigma_eph: float | None = None,
-            sigma_pp: float | None = None, v3_coef: float = 2.0e-8) -> Model:
+            sigma_pp: float | None = None, v3_coef: float = 2.0e-8, pp_stride: int = 1) -> Model:
     """Bulk-silicon-like 3D model (the precision-study workload): three conduction bands, band b
     being the pair of ellipsoidal valleys on axis b at +-0.85 of the zone half-width (m_l = 0.92,
     m_t = 0.19, lattice 5.43 Angstrom, simple cubic zone), states within `window` of the band
     minimum on an n^3 k-grid; six phonon branches (two TA and one LA Debye-like acoustic, three
-    flat ~60 meV optical) on the (n/fold)^3 q-grid, ph-ph on the full q-grid; hot electrons
+    flat ~60 meV optical) on the (n/fold)^3 q-grid, ph-ph on its stride-`pp_stride` sub-lattice
+    (the full q-grid by default); hot electrons
     at E_x over a 300 K Fermi-Dirac tail.  Broadenings default to the paper's 5 meV and 1.1 meV
     scaled by 80/n and 40/(n/fold) so that coarse grids keep resonant channels."""
     nk = (n, n, n)
@@ -399,7 +400,7 @@ def silicon(n: int = 32, fold: int = 2, window: float = 0.4, seed: int = SEED_BA
     N0[omega < 0.0002] = 0.0
     return Model(
         name=f"silicon_{n}_f{fold}", dim=3, nk=nk, nq=nq, fold=fold, nbands=3,
-        e_band=e_band, e_k=e_k, e_eps=e_eps, nmodes=6, ph_omega=omega, pp_stride=1,
+        e_band=e_band, e_k=e_k, e_eps=e_eps, nmodes=6, ph_omega=omega, pp_stride=pp_stride,
         sigma_eph=0.005 * 80.0 / n if sigma_eph is None else sigma_eph,
         sigma_pp=0.0011 * 40.0 / nq[0] if sigma_pp is None else sigma_pp, omega_cut=0.0002,
         g2_seed=seed, v3_seed=seed + 1000003, g2_coef=np.full(6, 1e-3), v3_coef=v3_coef,
@@ -407,6 +408,17 @@ def silicon(n: int = 32, fold: int = 2, window: float = 0.4, seed: int = SEED_BA
         integ=dict(t_end=20.0, h_s=0.050, rtol=1e-5, atol_c=1e-9, atol_ph=1e-11),
         note="config 3: silicon-like 3D, precision study (reduced grids)",
     )
+
+
+def silicon_printed() -> Model:
+    """The silicon-like workload at the printed grids: 80^3 k-grid, 0.4 eV window (36 321
+    states), six branches on the 40^3 q-grid (384 000 phonons), fold 2, ph-ph on the stride-2
+    sub-lattice (20^3 points, 48 000 phonons), the paper's 5 meV and 1.1 meV broadenings.
+    About 1.2e9 e-ph, 0.6e9 ph-e and 0.37e9 ph-ph stored entries (17.6 GB in FP32)."""
+    m = silicon(80, fold=2, pp_stride=2)
+    m.name = "silicon_80_f2_pp2"
+    m.note = "config 3: silicon-like 3D at the printed 80^3 / 40^3 grids, ph-ph on the stride-2 sub-lattice"
+    return m
 
 
 def ensemble(n_inst: int = 64, seed: int = SEED_BASE + 3, sides=tuple(range(24, 97, 3))) -> list:
@@ -440,5 +452,5 @@ def random_populations(model: Model, seed: int, spread: float = 1.0):
 
 def by_name(name: str, **kw) -> Model:
     table = {"toy2d": toy2d, "graphene": graphene, "graphene_small": graphene_small,
-             "ladder": ladder, "tiny": tiny, "silicon": silicon}
+             "ladder": ladder, "tiny": tiny, "silicon": silicon, "silicon_printed": silicon_printed}
     return table[name](**kw)

@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--accuracy-only", action="store_true", help="print only the error-versus-cost sweep")
     ap.add_argument("--surrogate-only", action="store_true", help="print only the learned slow-stage study")
     ap.add_argument("--silicon-only", action="store_true", help="print only the silicon-like precision study")
+    ap.add_argument("--printed-only", action="store_true",
+                    help="with --silicon-only: only the study at the printed 80^3/40^3 grids")
     ap.add_argument("--direct-launches", action="store_true",
                     help="integrator attempts by direct kernel launches instead of the device-loop graph "
                          "(same kernels; for per-kernel launch lists)")
@@ -437,6 +439,88 @@ def silicon_study(rt, ri, dev, n=32, t_end=0.5):
     return out
 
 
+def silicon_printed_study(rt, ri, dev, t_end=0.1):
+    """Config 3 at the printed grids (80^3 k-grid, 40^3 q-grid, ph-ph on the stride-2 sub-lattice;
+    ~2.1e9 stored entries): channel build, the collision kernel's roofline per part (FP32
+    compensated sums, e-ph lists in q-blocks so that every group is staged in shared memory) and
+    in FP64 (populations read from global memory: f alone exceeds shared memory), the FP32 RHS
+    against the FP64 one, and MRI (h_s = 50 fs, P:447 tolerances) over t_end in both precisions
+    plus the tolerance-chosen slow step in FP32."""
+    import numpy as np
+    import torch
+
+    m = ri.silicon_printed()
+    nc = m.n_c
+    y0 = torch.tensor(m.y0(), device=dev)
+    yr = torch.tensor(np.concatenate(ri.random_populations(m, 11)), device=dev)
+    tol = dict(rtol=1e-5, atol_c=1e-9, atol_ph=1e-11)
+    out = {"workload": f"silicon-like 3D at the printed grids: 3 bands on 80^3 k-grid within 0.4 eV ({nc} states), "
+                       f"6 branches on 40^3 q-grid ({m.n_ph} phonons), ph-ph on the stride-2 sub-lattice (20^3)",
+           "t_end_ps": t_end}
+    rhs = {}
+    finals = {}
+    for prec in ("fp32", "fp64"):
+        c = rt.Context(m, precision=prec, device=dev.index or 0)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        c.upload_channels()
+        torch.cuda.synchronize()
+        sz = c.sizes(0)
+        ent = {"eph": sz["eph_entries"], "phe": sz["phe_entries"], "pp": sz["pp_entries"]}
+        ent["all"] = sum(ent.values())
+        bpe = 8 if prec == "fp32" else 12
+        res = {"channel_build_s": time.time() - t0, "entries": ent["all"], "eph_q_blocks": sz["eph_q_blocks"],
+               "channel_bytes": sz["channel_bytes"], "parts": {}}
+        yd = torch.empty_like(y0)
+        c.rhs(y0, yd)
+        for name, mask in (("eph", rt.RTBTE_EPH), ("phe", rt.RTBTE_PHE), ("pp", rt.RTBTE_PHPH), ("all", rt.RTBTE_ALL)):
+            if prec == "fp64" and name != "all":
+                continue
+            c.autotune(mask)
+            for _ in range(2):
+                c.rhs(y0, yd, parts=mask)
+            torch.cuda.synchronize()
+            c.set_kernel_timing(True)
+            c.kernel_time()
+            for _ in range(5 if prec == "fp32" else 2):
+                c.rhs(y0, yd, parts=mask)
+            kms, kn = c.kernel_time()
+            c.set_kernel_timing(False)
+            gbs = bpe * ent[name] / (kms / kn) / 1e6
+            res["parts"][name] = {"rhs_kernel_ms": kms / kn, "achieved_gbs": gbs}
+        rhs[prec] = [c.rhs(y, parts=rt.RTBTE_ALL).cpu().numpy() for y in (y0, yr)]
+        runs = []
+        fams = [("mri", dict(method="mri", h_s=0.050, **tol))]
+        if prec == "fp32":
+            fams.append(("mri_adapt", dict(method="mri_adapt", h_s=0.050, fast_tol_scale=1.0, **tol)))
+        for fam, kw in fams:
+            y = y0.clone()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(c.stream)
+            st = c.advance_to(t_end, y, t0=0.0, **kw)
+            e1.record(c.stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1000.0
+            finals[(prec, fam)] = y.cpu().numpy()
+            runs.append({"method": fam, "status": st["status"], "seconds": sec, "sim_ps_per_s": t_end / sec,
+                         "rhs_fast": st["rhs_fast"], "rhs_slow": st["rhs_slow"], "slow_steps": st["slow_steps"],
+                         "slow_fails": st["slow_fails"]})
+        res["runs"] = runs
+        out[prec] = res
+        c.close()
+
+    def rel(a, b, sl):
+        return float(np.linalg.norm(a[sl] - b[sl]) / np.linalg.norm(b[sl]))
+
+    out["rhs_fp32_vs_fp64"] = [{"state": nm, "carriers": rel(a, b, slice(0, nc)), "phonons": rel(a, b, slice(nc, None))}
+                               for nm, a, b in zip(("y0", "random"), rhs["fp32"], rhs["fp64"])]
+    ref = finals[("fp64", "mri")]
+    out["mri_vs_fp64_mri"] = {f"{p}_{f}": {"carriers": rel(v, ref, slice(0, nc)), "phonons": rel(v, ref, slice(nc, None))}
+                              for (p, f), v in finals.items() if (p, f) != ("fp64", "mri")}
+    return out
+
+
 def surrogate_study(rt, ri, dev, t_end=0.5, h_s=0.020, period=10):
     """The learned slow stage on the same workload and error protocol.  Pairs (N, exact
     I^{ph-ph}) come from the method's own trajectories (6 initial conditions, 21 states
@@ -674,6 +758,8 @@ def run_ours(args):
 
     # ---- config 3: silicon-like 3D precision study
     si = silicon_study(rt, ri, dev) if (rank == 0 and not args.no_silicon) else None
+    if si is not None:
+        si["printed_grids"] = silicon_printed_study(rt, ri, dev)
 
     if rank == 0:
         cpu = None
@@ -727,7 +813,10 @@ def main():
         import paper_2412_13402_gb300 as rt
         import rtbte_inputs as ri
 
-        print(json.dumps(silicon_study(rt, ri, torch.device("cuda", 0))), flush=True)
+        dev = torch.device("cuda", 0)
+        out = silicon_study(rt, ri, dev) if not args.printed_only else {}
+        out["printed_grids"] = silicon_printed_study(rt, ri, dev)
+        print(json.dumps(out), flush=True)
         return 0
     if args.surrogate_only:
         import torch

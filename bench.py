@@ -64,18 +64,21 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: only standalone full-RHS evaluations (warm-up + steps), no JSON line")
     ap.add_argument("--grid", type=int, default=180, help="k/q grid side of the graphene-like workload (profiling)")
+    ap.add_argument("--workload", default="graphene", choices=["graphene", "silicon_printed"],
+                    help="workload of --profile: the graphene-like one at --grid, or config 3 at the printed grids")
     return ap.parse_args()
 
 
 def run_profile(args):
     """Standalone collision-kernel launches for ncu captures: `--warmup` then `--steps` full-RHS
-    evaluations of the graphene-like workload at grid side `--grid`."""
+    evaluations of the graphene-like workload at grid side `--grid`, or (`--workload
+    silicon_printed`) of the silicon-like workload at the printed 80^3 / 40^3 grids."""
     import torch
 
     import paper_2412_13402_gb300 as rt
     import rtbte_inputs as ri
 
-    m = ri.graphene(n=args.grid)
+    m = ri.graphene(n=args.grid) if args.workload == "graphene" else ri.silicon_printed()
     ctx = rt.Context(m, precision="fp32")
     ctx.upload_channels()
     y = torch.tensor(m.y0(), device="cuda")
@@ -90,7 +93,7 @@ def run_profile(args):
         ctx.rhs(y, yd)
     ms, n = ctx.kernel_time()
     s = ctx.sizes(0)
-    print(f"profile grid={args.grid} entries={s['eph_entries'] + s['phe_entries'] + s['pp_entries']} "
+    print(f"profile workload={m.name} entries={s['eph_entries'] + s['phe_entries'] + s['pp_entries']} "
           f"tuning={ctx.tuning()} rhs_kernel_avg_ms={ms / max(n, 1):.4f}", flush=True)
     ctx.close()
     return 0

@@ -223,9 +223,9 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
 
 
-def traffic_from_profile(kernel_src):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
-    path = os.path.join(ROOT, "profiles", "rhs_kernel_graphene180_dram.txt")
+def traffic_from_profile(kernel_src, summary="rhs_kernel_graphene180_dram.txt"):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on this kernel source."""
+    path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
     sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
@@ -491,6 +491,10 @@ def silicon_printed_study(rt, ri, dev, t_end=0.1):
             c.set_kernel_timing(False)
             gbs = bpe * ent[name] / (kms / kn) / 1e6
             res["parts"][name] = {"rhs_kernel_ms": kms / kn, "achieved_gbs": gbs}
+            if prec == "fp32" and name == "all":
+                res["parts"][name]["traffic"] = traffic_from_profile(
+                    os.path.join(ROOT, "paper_2412_13402_gb300", "csrc", "rhs.cu"), "rhs_kernel_silicon_printed_dram.txt")
+                res["parts"][name]["alg_bytes"] = bpe * ent[name]
         rhs[prec] = [c.rhs(y, parts=rt.RTBTE_ALL).cpu().numpy() for y in (y0, yr)]
         runs = []
         fams = [("mri", dict(method="mri", h_s=0.050, **tol))]

@@ -109,3 +109,28 @@ def test_q_blocked_integration_follows_the_unblocked_one(rt):
     (ya, sa, fa), (yb, sb, fb) = runs
     assert (sa, fa) == (sb, fb)
     assert relL2(yb, ya) < 1e-12
+
+
+def test_fp64_graphene_180_takes_q_blocks_and_matches_literal_rows(rt, oracle_lib):
+    """FP64 on the 180 x 180 graphene-like workload: f (102 KB) and one mode's N (259 KB) exceed
+    shared memory, so the build takes two q-blocks per mode automatically; sampled rows of
+    every family within the FP64 parity tolerance (1e-12) of the oracle's literal sums."""
+    m = ri.graphene()
+    ctx = rt.Context(m, precision="fp64")
+    ctx.upload_channels()
+    assert ctx.sizes(0)["eph_q_blocks"] == 2
+    o = oracle_lib.Oracle(m)
+    rng = np.random.default_rng(4)
+    y = np.concatenate(ri.random_populations(m, 21))
+    e_rows = rng.choice(m.n_c, 16, replace=False)
+    full = o.pp_full_index()
+    p_rows = np.unique(np.concatenate([rng.choice(m.n_ph, 16, replace=False), full[rng.choice(len(full), 16, replace=False)]]))
+    em = np.zeros(m.n_c, np.uint8)
+    pm = np.zeros(m.n_ph, np.uint8)
+    em[e_rows] = 1
+    pm[p_rows] = 1
+    ref = o.rhs_literal(y, ALL, em, pm)
+    got = ctx.rhs(torch.tensor(y, device="cuda")).cpu().numpy()
+    assert relL2(got[e_rows], ref[e_rows]) <= 1e-12
+    assert relL2(got[m.n_c + p_rows], ref[m.n_c + p_rows]) <= 1e-12
+    ctx.close()

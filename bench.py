@@ -338,9 +338,9 @@ def accuracy_sweep(rt, ri, dev, t_end=0.5):
     settings = [("fp32", "erk", dict(method="zon43", rtol=r, atol_c=1e-15, atol_ph=1e-15)) for r in
                 (1e-4, 1e-5, 1e-6, 1e-7)]
     settings += [("fp32", "mri", dict(method="mri", h_s=hs * 1e-3, rtol=r, atol_c=1e-9, atol_ph=1e-12))
-                 for hs in (50.0, 20.0, 10.0) for r in (1e-5, 1e-6)]
+                 for hs in (100.0, 50.0, 20.0, 10.0) for r in (1e-4, 1e-5, 1e-6)]
     settings += [("fp32", "mri_adapt", dict(method="mri_adapt", h_s=20e-3, rtol=r, atol_c=1e-9, atol_ph=1e-12,
-                                            fast_tol_scale=fts)) for fts in (0.1, 1.0) for r in (1e-5, 1e-6)]
+                                            fast_tol_scale=fts)) for fts in (0.1, 1.0) for r in (1e-4, 1e-5, 1e-6)]
     settings += [("fp32", "rk4", dict(method="rk4", h=h * 1e-3)) for h in (5.0, 2.0, 1.0)]
     settings += [("fp64", "erk", dict(method="zon43", rtol=r, atol_c=1e-15, atol_ph=1e-15)) for r in (1e-5, 1e-6)]
     settings += [("fp64", "mri", dict(method="mri", h_s=20e-3, rtol=1e-6, atol_c=1e-9, atol_ph=1e-12))]

@@ -18,7 +18,7 @@
  *     step controller (Eq. pid_controller), and the explicit MRI/MIS algorithm
  *     (Methods B, Eq. mis_coef), plus first-order RK4 operator splitting.
  *
- * Readings where the paper is silent or garbled (each also listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - Gaussian delta: exp(-(E/sigma)^2)/(sigma*sqrt(pi)), truncated at |E|>3 sigma
  *     (the printed form in Methods A is not normalisable).
  *   - MIS last-stage coupling uses b_j - A_{S,j} (the printed A_{S-1,j} breaks
@@ -26,6 +26,8 @@
  *   - PID exponents alternate in sign (-a1, +a2, -a3), ARKODE's documented form;
  *     the all-negative printed form is selectable.
  *   - Controller constants not in the paper follow ARKODE's documented defaults.
+ *   - The slow step of the tolerance-chosen MRI (future work in the Discussion) is
+ *     controlled by step doubling with library constants (or_mri_adapt_solve).
  *
  * Parity pins: see tests/test_oracle_*.py (detailed balance, conservation laws,
  * brute force, closed-form ODE solutions, order conditions).

@@ -336,9 +336,9 @@ def accuracy_sweep(rt, ri, dev, t_end=0.5):
         return float(ec), float(ep)
 
     settings = [("fp32", "erk", dict(method="zon43", rtol=r, atol_c=1e-15, atol_ph=1e-15)) for r in
-                (1e-4, 1e-5, 1e-6, 1e-7)]
+                (3e-4, 1e-4, 1e-5, 1e-6, 1e-7)]
     settings += [("fp32", "mri", dict(method="mri", h_s=hs * 1e-3, rtol=r, atol_c=1e-9, atol_ph=1e-12))
-                 for hs in (100.0, 50.0, 20.0, 10.0) for r in (1e-4, 1e-5, 1e-6)]
+                 for hs in (150.0, 100.0, 70.0, 50.0, 20.0, 10.0) for r in (3e-4, 1e-4, 1e-5, 1e-6)]
     settings += [("fp32", "mri_adapt", dict(method="mri_adapt", h_s=20e-3, rtol=r, atol_c=1e-9, atol_ph=1e-12,
                                             fast_tol_scale=fts)) for fts in (0.1, 1.0) for r in (1e-4, 1e-5, 1e-6)]
     settings += [("fp32", "rk4", dict(method="rk4", h=h * 1e-3)) for h in (5.0, 2.0, 1.0)]

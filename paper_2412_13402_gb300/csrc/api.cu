@@ -249,7 +249,11 @@ int download(rtbte_ctx *ctx, InstHost &I, unsigned which, int64_t *off, int32_t 
                 }
         return RTBTE_OK;
     }
+    std::vector<long long> ord;
+    std::vector<int32_t> ta, tb;
+    std::vector<double> tw;
     for (long long g = 0; g < nseg; ++g) {
+        const long long o0 = o;
         for (long long k = 0; k < (*cn)[g]; ++k) {
             const uint32_t e = hidx[(*po)[g] + k];
             if (which == RTBTE_EPH) {
@@ -265,6 +269,28 @@ int download(rtbte_ctx *ctx, InstHost &I, unsigned which, int64_t *off, int32_t 
             }
             W[o] = (double)hW[(*po)[g] + k];
             ++o;
+        }
+        // stored blocks are in bank-aware order: hand the segment back sorted by (a, b)
+        const long long n = o - o0;
+        if (n > 1) {
+            ord.resize(n);
+            for (long long i = 0; i < n; ++i) ord[i] = o0 + i;
+            std::sort(ord.begin(), ord.end(), [&](long long x, long long y) {
+                return a[x] != a[y] ? a[x] < a[y] : b[x] < b[y];
+            });
+            ta.resize(n);
+            tb.resize(n);
+            tw.resize(n);
+            for (long long i = 0; i < n; ++i) {
+                ta[i] = a[ord[i]];
+                tb[i] = b[ord[i]];
+                tw[i] = W[ord[i]];
+            }
+            for (long long i = 0; i < n; ++i) {
+                a[o0 + i] = ta[i];
+                b[o0 + i] = tb[i];
+                W[o0 + i] = tw[i];
+            }
         }
         off[g + 1] = o;
     }

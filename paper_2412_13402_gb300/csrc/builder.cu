@@ -338,6 +338,75 @@ template <class T> int dev_upload(rtbte_ctx *ctx, DevBuf &b, const std::vector<T
     return RTBTE_OK;
 }
 
+// Bank-aware entry order.  The collision kernel gives lane l of a warp the 16-byte vector l of
+// each 128-entry block of an item and gathers, for component k of every vector, two populations
+// from shared memory per entry; 32 lanes whose gather addresses share a bank serialise.  Each
+// full block of a segment that lies inside its logical entries (blocks counted from the segment
+// start, as the work items are) is reordered so that position 4*l + k holds the entry a greedy
+// assigns to lane l and component k: entries in built order, each to the component whose lanes
+// so far use neither of its two banks (else the one with fewer clashes, then the lowest).  The
+// block holding the segment's last logical entry and its padding keeps the built order, so
+// padding stays at the segment end.  Sums over a segment do not depend on its entry order
+// beyond rounding; rtbte_download_channels returns every segment in its sorted order.
+template <class R>
+__global__ void bank_order(uint32_t *idx, R *W, const long long *off, const long long *cnt, long long nseg, int part,
+                           int lo_bits, int nc, int nqb, int qblk, int l0) {
+    const long long seg = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (seg >= nseg) return;
+    constexpr int NB = sizeof(R) == 4 ? 32 : 16;  // banks per shared-memory element size
+    const long long b0 = off[seg], n = cnt[seg];
+    const unsigned lmask = (1u << lo_bits) - 1u;
+    int offB = 0;  // element offset of the second gather's array in shared memory
+    if (part == PART_EPH) {
+        const long long blk = seg / (2LL * nc);
+        offB = l0 - (int)(blk % nqb) * qblk;
+    }
+    uint32_t ib[128];
+    R wb[128];
+    for (long long c0 = 0; c0 + 128 <= n; c0 += 128) {
+        for (int i = 0; i < 128; ++i) {
+            ib[i] = idx[b0 + c0 + i];
+            wb[i] = W[b0 + c0 + i];
+        }
+        unsigned mA[4] = {0u, 0u, 0u, 0u}, mB[4] = {0u, 0u, 0u, 0u};
+        int fill[4] = {0, 0, 0, 0};
+        for (int i = 0; i < 128; ++i) {
+            const uint32_t e = ib[i];
+            const int ba = (int)((e & lmask) % NB);
+            const int bb = (int)((((long long)(e >> lo_bits) + offB) % NB + NB) % NB);
+            int best = -1, cost = 3;
+            for (int k = 0; k < 4; ++k) {
+                if (fill[k] >= 32) continue;
+                const int c = (int)((mA[k] >> ba) & 1u) + (int)((mB[k] >> bb) & 1u);
+                if (c < cost) {
+                    cost = c;
+                    best = k;
+                }
+            }
+            const int lane = fill[best]++;
+            mA[best] |= 1u << ba;
+            mB[best] |= 1u << bb;
+            if (fill[best] == 32) mA[best] = mB[best] = ~0u;  // full: never chosen again
+            const long long at = b0 + c0 + 4 * lane + best;
+            idx[at] = e;
+            W[at] = wb[i];
+        }
+    }
+}
+
+template <class R>
+int order_banks(rtbte_ctx *ctx, const InstHost &I, int part, DevBuf &idx, DevBuf &W, const DevBuf &off,
+                const DevBuf &cnt, long long nseg) {
+    if (nseg <= 0) return RTBTE_OK;
+    const int lo_bits = part == PART_PP ? I.pp_bits : I.s_bits;
+    bank_order<R><<<(unsigned)((nseg + 127) / 128), 128, 0, ctx->stream>>>(
+        idx.as<uint32_t>(), W.as<R>(), off.as<long long>(), cnt.as<long long>(), nseg, part, lo_bits, I.d.n_c,
+        std::max(I.eph_nqb, 1), I.eph_qblk > 0 ? I.eph_qblk : I.N_q_pad, I.n_c_pad);
+    RT_CUDA(ctx, cudaGetLastError());
+    ctx->launches++;
+    return RTBTE_OK;
+}
+
 // counts -> padded offsets; returns total stored entries
 long long pad_offsets(const std::vector<long long> &cnt, std::vector<long long> &off) {
     off.assign(cnt.size() + 1, 0);
@@ -439,6 +508,8 @@ int run_build(rtbte_ctx *ctx, InstHost &I) {
         T, nullptr, off.as<long long>(), I.eph_idx.as<uint32_t>(), I.eph_W.p);
     RT_CUDA(ctx, cudaGetLastError());
     ctx->launches++;
+    int rc;
+    if ((rc = order_banks<R>(ctx, I, PART_EPH, I.eph_idx, I.eph_W, off, cnt, nseg))) return rc;
     RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     cnt.release();
     off.release();
@@ -464,6 +535,7 @@ int run_build(rtbte_ctx *ctx, InstHost &I) {
         T, nullptr, off.as<long long>(), I.phe_idx.as<uint32_t>(), I.phe_W.p);
     RT_CUDA(ctx, cudaGetLastError());
     ctx->launches++;
+    if ((rc = order_banks<R>(ctx, I, PART_PHE, I.phe_idx, I.phe_W, off, cnt, nph))) return rc;
     RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     cnt.release();
     off.release();
@@ -493,6 +565,7 @@ int run_build(rtbte_ctx *ctx, InstHost &I) {
             T, nullptr, off.as<long long>(), I.pp_idx.as<uint32_t>(), I.pp_W.p);
         RT_CUDA(ctx, cudaGetLastError());
         ctx->launches++;
+        if ((rc = order_banks<R>(ctx, I, PART_PP, I.pp_idx, I.pp_W, off, cnt, ns))) return rc;
         RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         cnt.release();
         off.release();

@@ -223,18 +223,26 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
 
 
-def traffic_from_profile(kernel_src, summary="rhs_kernel_graphene180_dram.txt"):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on this kernel source."""
+def kernel_sources_sha():
+    """Hash of the sources that decide the collision kernel's memory traffic: the kernel and
+    plan (rhs.cu) and the channel builder that lays out the entries it streams (builder.cu)."""
+    h = hashlib.sha256()
+    for f in ("rhs.cu", "builder.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2412_13402_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(summary="rhs_kernel_graphene180_dram.txt"):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current sources."""
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
-    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(path):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("rhs_cu_sha256_16") != sha:
+    if vals.get("kernel_sources_sha256_16") != kernel_sources_sha():
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -492,8 +500,7 @@ def silicon_printed_study(rt, ri, dev, t_end=0.1):
             gbs = bpe * ent[name] / (kms / kn) / 1e6
             res["parts"][name] = {"rhs_kernel_ms": kms / kn, "achieved_gbs": gbs}
             if prec == "fp32" and name == "all":
-                res["parts"][name]["traffic"] = traffic_from_profile(
-                    os.path.join(ROOT, "paper_2412_13402_gb300", "csrc", "rhs.cu"), "rhs_kernel_silicon_printed_dram.txt")
+                res["parts"][name]["traffic"] = traffic_from_profile("rhs_kernel_silicon_printed_dram.txt")
                 res["parts"][name]["alg_bytes"] = bpe * ent[name]
         rhs[prec] = [c.rhs(y, parts=rt.RTBTE_ALL).cpu().numpy() for y in (y0, yr)]
         runs = []
@@ -714,7 +721,7 @@ def run_ours(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = alg_bytes / avg_s / 1e9
-    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2412_13402_gb300", "csrc", "rhs.cu"))
+    traffic = traffic_from_profile()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "rhs_kernel (full RHS: e-ph + ph-e + ph-ph)",
                 "avg_launch_ms": avg_s * 1000.0, "launches_timed": kn, "alg_bytes_per_launch": alg_bytes,

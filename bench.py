@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--accuracy-only", action="store_true", help="print only the error-versus-cost sweep")
     ap.add_argument("--surrogate-only", action="store_true", help="print only the learned slow-stage study")
     ap.add_argument("--silicon-only", action="store_true", help="print only the silicon-like precision study")
+    ap.add_argument("--silicon-long", action="store_true",
+                    help="print only config 3 at the printed grids integrated to 20 ps (FP32; FP64 first ps)")
     ap.add_argument("--printed-only", action="store_true",
                     help="with --silicon-only: only the study at the printed 80^3/40^3 grids")
     ap.add_argument("--direct-launches", action="store_true",
@@ -535,6 +537,71 @@ def silicon_printed_study(rt, ri, dev, t_end=0.1):
     return out
 
 
+def silicon_long_study(rt, ri, dev, t_end=20.0, window=1.0):
+    """Config 3's integration length at the printed grids: MRI (h_s = 50 fs, P:447 tolerances)
+    with FP32 compensated sums to t_end in windows (controller resumed across windows), with
+    the mean excess energy of the carriers and the phonon energy per window; FP64 over the
+    first window for the precision comparison at that time."""
+    import numpy as np
+    import torch
+
+    m = ri.silicon_printed()
+    nc = m.n_c
+    eps = np.asarray(m.e_eps)
+    om = np.asarray(m.ph_omega)
+    nq = float(np.prod(m.nq))
+    tol = dict(rtol=1e-5, atol_c=1e-9, atol_ph=1e-11)
+
+    def observables(y):
+        f, N = y[:nc], y[nc:]
+        return {"carrier_mean_energy_eV": float((eps * f).sum() / f.sum()),
+                "phonon_energy_eV_per_cell": float((om * N).sum() / nq)}
+
+    out = {"workload": "silicon-like 3D at the printed grids (80^3 / 40^3, ph-ph on the stride-2 sub-lattice)",
+           "method": "MRI h_s 50 fs, rtol 1e-5, atol_c 1e-9, atol_ph 1e-11", "t_end_ps": t_end, "window_ps": window}
+    c = rt.Context(m, precision="fp32", device=dev.index or 0)
+    c.upload_channels()
+    y = torch.tensor(m.y0(), device=dev)
+    c.rhs(y, torch.empty_like(y))
+    c.autotune(rt.RTBTE_ALL)
+    wins, t, y1 = [], 0.0, None
+    obs0 = observables(m.y0())
+    while t < t_end - 1e-12:
+        t1 = min(t + window, t_end)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(c.stream)
+        st = c.advance_to(t1, y, method="mri", t0=t, h_s=0.050, resume=1 if t > 0 else 0, **tol)
+        e1.record(c.stream)
+        torch.cuda.synchronize()
+        assert st["status"] == 0, st
+        yh = y.cpu().numpy()
+        if y1 is None:
+            y1 = yh.copy()
+        wins.append({"t_ps": t1, "seconds": e0.elapsed_time(e1) / 1000.0, "fast_steps": st["steps"],
+                     "slow_steps": st["slow_steps"], "rhs_fast": st["rhs_fast"], "rhs_slow": st["rhs_slow"],
+                     **observables(yh)})
+        t = t1
+    c.close()
+    total = sum(w["seconds"] for w in wins)
+    out.update({"initial": obs0, "windows": wins, "seconds": total, "sim_ps_per_s": t_end / total})
+    c = rt.Context(m, precision="fp64", device=dev.index or 0)
+    c.upload_channels()
+    y = torch.tensor(m.y0(), device=dev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(c.stream)
+    st = c.advance_to(window, y, method="mri", t0=0.0, h_s=0.050, **tol)
+    e1.record(c.stream)
+    torch.cuda.synchronize()
+    y64 = y.cpu().numpy()
+    c.close()
+    out["fp64_first_window"] = {"status": st["status"], "seconds": e0.elapsed_time(e1) / 1000.0,
+                                "fp32_vs_fp64_carriers": float(np.linalg.norm(y1[:nc] - y64[:nc]) / np.linalg.norm(y64[:nc])),
+                                "fp32_vs_fp64_phonons": float(np.linalg.norm(y1[nc:] - y64[nc:]) / np.linalg.norm(y64[nc:]))}
+    return out
+
+
 def surrogate_study(rt, ri, dev, t_end=0.5, h_s=0.020, period=10):
     """The learned slow stage on the same workload and error protocol.  Pairs (N, exact
     I^{ph-ph}) come from the method's own trajectories (6 initial conditions, 21 states
@@ -820,6 +887,14 @@ def main():
         import rtbte_inputs as ri
 
         print(json.dumps(accuracy_sweep(rt, ri, torch.device("cuda", 0))), flush=True)
+        return 0
+    if args.silicon_long:
+        import torch
+
+        import paper_2412_13402_gb300 as rt
+        import rtbte_inputs as ri
+
+        print(json.dumps(silicon_long_study(rt, ri, torch.device("cuda", 0))), flush=True)
         return 0
     if args.silicon_only:
         import torch

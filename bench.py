@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--accuracy-only", action="store_true", help="print only the error-versus-cost sweep")
     ap.add_argument("--surrogate-only", action="store_true", help="print only the learned slow-stage study")
     ap.add_argument("--silicon-only", action="store_true", help="print only the silicon-like precision study")
+    ap.add_argument("--graphene-long", action="store_true",
+                    help="print only the graphene-like workload integrated to 100 ps (ERK and MRI, FP32)")
     ap.add_argument("--silicon-long", action="store_true",
                     help="print only config 3 at the printed grids integrated to 20 ps (FP32; FP64 first ps)")
     ap.add_argument("--printed-only", action="store_true",
@@ -537,6 +539,64 @@ def silicon_printed_study(rt, ri, dev, t_end=0.1):
     return out
 
 
+def graphene_long_study(rt, ri, dev, t_end=100.0, window=5.0):
+    """Config 2's integration length: the graphene-like workload to t_end with adaptive Zonneveld
+    and with MRI (h_s = 20 fs; P:553 tolerances), FP32 compensated sums, in windows (controllers
+    resumed); per window the wall time, the conduction electrons' mean excess energy and the mean
+    occupation of the highest optical branch (LO) and of the acoustic branches -- the quantities
+    of the paper's qualitative picture (carriers cool within ~1 ps, optical phonons are emitted
+    and then decay into acoustic ones) -- and the two methods' difference at t_end."""
+    import numpy as np
+    import torch
+
+    m = ri.graphene()
+    nc = m.n_c
+    eps = np.asarray(m.e_eps)
+    cond = eps > 0
+    nq = int(np.prod(m.nq))
+    N_lo = slice(5 * nq, 6 * nq)
+    N_ac = slice(0, 3 * nq)
+    tol = dict(rtol=1e-5, atol_c=1e-9, atol_ph=1e-12)
+
+    def observables(y):
+        f, N = y[:nc], y[nc:]
+        return {"electron_mean_excess_eV": float((eps[cond] * f[cond]).sum() / f[cond].sum()),
+                "N_LO_mean": float(N[N_lo].mean()), "N_acoustic_mean": float(N[N_ac].mean())}
+
+    out = {"workload": "graphene-like 180x180", "t_end_ps": t_end, "window_ps": window,
+           "initial": observables(m.y0())}
+    c = rt.Context(m, precision="fp32", device=dev.index or 0)
+    c.upload_channels()
+    y0 = torch.tensor(m.y0(), device=dev)
+    c.rhs(y0, torch.empty_like(y0))
+    c.autotune(rt.RTBTE_ALL)
+    finals = {}
+    for fam, kw in (("erk", dict(method="zon43", **tol)), ("mri", dict(method="mri", h_s=0.020, **tol))):
+        y = y0.clone()
+        t, wins = 0.0, []
+        # the first picosecond finer, where the carriers cool
+        edges = [0.1, 0.25, 0.5, 1.0] + list(np.arange(window, t_end + 1e-9, window))
+        for t1 in edges:
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(c.stream)
+            st = c.advance_to(float(t1), y, t0=t, resume=1 if t > 0 else 0, **kw)
+            e1.record(c.stream)
+            torch.cuda.synchronize()
+            assert st["status"] == 0, (fam, st)
+            wins.append({"t_ps": float(t1), "seconds": e0.elapsed_time(e1) / 1000.0, "steps": st["steps"],
+                         **observables(y.cpu().numpy())})
+            t = float(t1)
+        finals[fam] = y.cpu().numpy()
+        total = sum(w["seconds"] for w in wins)
+        out[fam] = {"seconds": total, "sim_ps_per_s": t_end / total, "windows": wins}
+    c.close()
+    a, b = finals["mri"], finals["erk"]
+    out["mri_vs_erk_at_t_end"] = {"carriers": float(np.linalg.norm(a[:nc] - b[:nc]) / np.linalg.norm(b[:nc])),
+                                  "phonons": float(np.linalg.norm(a[nc:] - b[nc:]) / np.linalg.norm(b[nc:]))}
+    return out
+
+
 def silicon_long_study(rt, ri, dev, t_end=20.0, window=1.0):
     """Config 3's integration length at the printed grids: MRI (h_s = 50 fs, P:447 tolerances)
     with FP32 compensated sums to t_end in windows (controller resumed across windows), with
@@ -887,6 +947,14 @@ def main():
         import rtbte_inputs as ri
 
         print(json.dumps(accuracy_sweep(rt, ri, torch.device("cuda", 0))), flush=True)
+        return 0
+    if args.graphene_long:
+        import torch
+
+        import paper_2412_13402_gb300 as rt
+        import rtbte_inputs as ri
+
+        print(json.dumps(graphene_long_study(rt, ri, torch.device("cuda", 0))), flush=True)
         return 0
     if args.silicon_long:
         import torch

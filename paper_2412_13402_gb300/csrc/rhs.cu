@@ -494,17 +494,40 @@ __global__ void __launch_bounds__(kRhsThreads, MINB) rhs_kernel(KParams P) {
 __global__ void split_kernel(const Group *groups, int n_groups, const long long *wpre, const Ctl *ctl, unsigned mask,
                              int grid, int n_items, int *out) {
     __shared__ long long A[1025];
-    const int T = blockDim.x;
-    // active weight of each group; n_groups <= 1024 (checked on the host)
-    for (int g = threadIdx.x; g < n_groups; g += T) {
+    __shared__ long long wsum[32];
+    const int T = blockDim.x;  // 256 threads, n_groups <= 1024 (checked on the host)
+    // active weight of each group, then an inclusive prefix over the groups: each thread scans
+    // a run of C consecutive groups, the run totals are scanned across the block (warp
+    // shuffles, then the warp totals), and each run adds the total before it
+    const int C = (n_groups + T - 1) / T;
+    const int g0 = threadIdx.x * C;
+    long long run = 0;
+    for (int g = g0; g < g0 + C && g < n_groups; ++g) {
         const Group &G = groups[g];
         const bool on = (mask & (1u << G.part)) && !ctl[G.inst].done;
-        A[g + 1] = on ? wpre[G.item_end] - wpre[G.item_begin] : 0;
+        run += on ? wpre[G.item_end] - wpre[G.item_begin] : 0;
+        A[g + 1] = run;
     }
-    if (threadIdx.x == 0) {
-        A[0] = 0;
-        for (int g = 0; g < n_groups; ++g) A[g + 1] += A[g];  // a few hundred groups: serial scan
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long incl = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
     }
+    if (lane == 31) wsum[wid] = incl;
+    if (threadIdx.x == 0) A[0] = 0;
+    __syncthreads();
+    if (wid == 0) {
+        long long w = lane < (T >> 5) ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long v = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += v;
+        }
+        if (lane < (T >> 5)) wsum[lane] = w;
+    }
+    __syncthreads();
+    const long long before = incl - run + (wid > 0 ? wsum[wid - 1] : 0);
+    for (int g = g0; g < g0 + C && g < n_groups; ++g) A[g + 1] += before;
     __syncthreads();
     const long long total = A[n_groups];
     for (int c = threadIdx.x; c <= grid; c += T) {

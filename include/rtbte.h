@@ -286,6 +286,12 @@ int rtbte_get_sizes(const rtbte_ctx *ctx, int inst, rtbte_sizes *out);
  * count + 1 entries (e-ph 2*nmodes*n_c, ph-e n_ph, ph-ph 2*n_pp); a/b/W must hold the logical
  * entry count (rtbte_get_sizes).  For e-ph a/b are (src, phonon); ph-e (dst, src); ph-ph
  * (b, c).  Synchronous. */
+/* The same for the segments [seg_begin, seg_end) of that order only (for lists too large to
+ * copy back whole): off receives seg_end - seg_begin + 1 offsets relative to the first; with
+ * a = NULL only off is filled (to size a/b/W), else a/b/W hold `cap` entries at most.
+ * Synchronous.  Errors: INVALID_ARG (range, capacity), STATE (no channels), CUDA. */
+int rtbte_download_segments(rtbte_ctx *ctx, int inst, unsigned which, int64_t seg_begin, int64_t seg_end, int64_t *off,
+                            int32_t *a, int32_t *b, double *W, int64_t cap);
 int rtbte_download_channels(rtbte_ctx *ctx, int inst, unsigned which, int64_t *off, int32_t *a, int32_t *b,
                             double *W);
 

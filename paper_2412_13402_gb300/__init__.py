@@ -33,7 +33,7 @@ RTBTE_RK4, RTBTE_BS32, RTBTE_ZON43, RTBTE_MRI_KW3, RTBTE_SPLIT_RK4, RTBTE_MRI_AD
 HBAR_EV_PS = 6.582119569e-4
 
 EXPORTS = ["rtbte_desc_defaults", "rtbte_integ_defaults", "rtbte_create", "rtbte_upload_channels", "rtbte_rhs",
-           "rtbte_advance_to", "rtbte_get_controller", "rtbte_set_controller", "rtbte_phph_rates", "rtbte_get_sizes", "rtbte_download_channels", "rtbte_set_stream",
+           "rtbte_advance_to", "rtbte_get_controller", "rtbte_set_controller", "rtbte_phph_rates", "rtbte_get_sizes", "rtbte_download_channels", "rtbte_download_segments", "rtbte_set_stream",
            "rtbte_autotune", "rtbte_get_tuning", "rtbte_set_graph_mode", "rtbte_set_kernel_timing", "rtbte_kernel_time", "rtbte_launch_count", "rtbte_last_error",
            "rtbte_status_string", "rtbte_eph_rhs_noalloc", "rtbte_surrogate_create", "rtbte_surrogate_collect",
            "rtbte_surrogate_train", "rtbte_surrogate_predict", "rtbte_surrogate_loss_grad",
@@ -131,6 +131,7 @@ def load():
         L.rtbte_set_controller.argtypes = [vp, i32, vp]
         L.rtbte_get_sizes.argtypes = [vp, i32, vp]
         L.rtbte_download_channels.argtypes = [vp, i32, C.c_uint, vp, vp, vp, vp]
+        L.rtbte_download_segments.argtypes = [vp, i32, C.c_uint, i64, i64, vp, vp, vp, vp, i64]
         L.rtbte_set_stream.argtypes = [vp, vp]
         L.rtbte_autotune.argtypes = [vp, C.c_uint, vp]
         L.rtbte_get_tuning.argtypes = [vp, vp, vp, vp]
@@ -309,6 +310,18 @@ class Context:
         off = np.zeros(nseg + 1, np.int64)
         a, b, W = np.zeros(max(E, 1), np.int32), np.zeros(max(E, 1), np.int32), np.zeros(max(E, 1), np.float64)
         _check(self.ctx, load().rtbte_download_channels(self.ctx, inst, which, _p(off), _p(a), _p(b), _p(W)))
+        return dict(off=off, a=a[:E], b=b[:E], W=W[:E])
+
+    def download_segments(self, inst: int, which: int, seg_begin: int, seg_end: int) -> dict:
+        """Segments [seg_begin, seg_end) of download_channels' order only (large lists)."""
+        L = load()
+        off = np.zeros(seg_end - seg_begin + 1, np.int64)
+        _check(self.ctx, L.rtbte_download_segments(self.ctx, inst, which, seg_begin, seg_end, _p(off), None, None,
+                                                   None, 0))
+        E = int(off[-1])
+        a, b, W = np.zeros(max(E, 1), np.int32), np.zeros(max(E, 1), np.int32), np.zeros(max(E, 1), np.float64)
+        _check(self.ctx, L.rtbte_download_segments(self.ctx, inst, which, seg_begin, seg_end, _p(off), _p(a), _p(b),
+                                                   _p(W), E))
         return dict(off=off, a=a[:E], b=b[:E], W=W[:E])
 
     # ---- compute ------------------------------------------------------------------

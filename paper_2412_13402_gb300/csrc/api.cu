@@ -297,6 +297,71 @@ int download(rtbte_ctx *ctx, InstHost &I, unsigned which, int64_t *off, int32_t 
     return RTBTE_OK;
 }
 
+// Segments [s0, s1) of the download order (e-ph (mode, electron, process), ph-e phonon, ph-ph
+// (sub-lattice phonon, process)), each copied from the device on its own and sorted by (a, b).
+template <class R>
+int download_range(rtbte_ctx *ctx, InstHost &I, unsigned which, long long s0, long long s1, int64_t *off, int32_t *a,
+                   int32_t *b, double *W, long long cap) {
+    const std::vector<long long> *po, *cn;
+    const DevBuf *di, *dw;
+    long long nseg;
+    if (which == RTBTE_EPH) { po = &I.eph_off; cn = &I.eph_cnt; di = &I.eph_idx; dw = &I.eph_W; nseg = 2LL * I.d.nmodes * I.d.n_c; }
+    else if (which == RTBTE_PHE) { po = &I.phe_off; cn = &I.phe_cnt; di = &I.phe_idx; dw = &I.phe_W; nseg = I.n_ph; }
+    else if (which == RTBTE_PHPH) { po = &I.pp_off; cn = &I.pp_cnt; di = &I.pp_idx; dw = &I.pp_W; nseg = 2 * I.M; }
+    else return fail(ctx, RTBTE_E_INVALID_ARG, "which must be RTBTE_EPH, RTBTE_PHE or RTBTE_PHPH");
+    if (s0 < 0 || s1 < s0 || s1 > nseg) return fail(ctx, RTBTE_E_INVALID_ARG, "segment range out of bounds");
+    RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const uint32_t smask = (1u << I.s_bits) - 1u, pmask = I.pp_bits ? (1u << I.pp_bits) - 1u : 0u;
+    const long long nc = I.d.n_c, nqb = which == RTBTE_EPH ? std::max(I.eph_nqb, 1) : 1;
+    std::vector<uint32_t> hidx;
+    std::vector<R> hW;
+    std::vector<std::pair<std::pair<int32_t, int32_t>, double>> seg;
+    long long o = 0;
+    off[0] = 0;
+    for (long long g = s0; g < s1; ++g) {
+        seg.clear();
+        for (long long qb = 0; qb < nqb; ++qb) {
+            long long sg = g;
+            if (which == RTBTE_EPH) sg = (((g / (2 * nc)) * nqb + qb) * nc + (g / 2) % nc) * 2 + g % 2;
+            const long long n = (*cn)[sg], at = (*po)[sg];
+            if (n == 0) continue;
+            hidx.resize(n);
+            hW.resize(n);
+            RT_CUDA(ctx, cudaMemcpy(hidx.data(), di->as<uint32_t>() + at, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+            RT_CUDA(ctx, cudaMemcpy(hW.data(), dw->as<R>() + at, n * sizeof(R), cudaMemcpyDeviceToHost));
+            for (long long k = 0; k < n; ++k) {
+                const uint32_t e = hidx[k];
+                int32_t x, y;
+                if (which == RTBTE_EPH) {
+                    x = (int32_t)(e & smask);
+                    y = (int32_t)((g / (2 * nc)) * I.N_q + (e >> I.s_bits));
+                } else if (which == RTBTE_PHE) {
+                    x = (int32_t)(e & smask);
+                    y = (int32_t)(e >> I.s_bits);
+                } else {
+                    x = (int32_t)(e & pmask);
+                    y = (int32_t)(e >> I.pp_bits);
+                }
+                seg.push_back({{x, y}, (double)hW[k]});
+            }
+        }
+        std::sort(seg.begin(), seg.end(), [](const auto &p, const auto &q) { return p.first < q.first; });
+        if (a) {
+            if (o + (long long)seg.size() > cap) return fail(ctx, RTBTE_E_INVALID_ARG, "entry arrays too small");
+            for (const auto &t : seg) {
+                a[o] = t.first.first;
+                b[o] = t.first.second;
+                W[o] = t.second;
+                ++o;
+            }
+        } else {
+            o += (long long)seg.size();
+        }
+        off[g - s0 + 1] = o;
+    }
+    return RTBTE_OK;
+}
+
 int ensure_plan(rtbte_ctx *ctx) {
     for (auto &I : ctx->inst)
         if (!I.has_channels) return fail(ctx, RTBTE_E_STATE, "an instance has no channels (call rtbte_upload_channels)");
@@ -531,6 +596,18 @@ int rtbte_download_channels(rtbte_ctx *ctx, int inst, unsigned which, int64_t *o
     if (!I.has_channels) return fail(ctx, RTBTE_E_STATE, "instance has no channels");
     return ctx->precision == RTBTE_PREC_FP64 ? download<double>(ctx, I, which, off, a, b, W)
                                              : download<float>(ctx, I, which, off, a, b, W);
+}
+
+int rtbte_download_segments(rtbte_ctx *ctx, int inst, unsigned which, int64_t seg_begin, int64_t seg_end, int64_t *off,
+                            int32_t *a, int32_t *b, double *W, int64_t cap) {
+    if (!ctx) return RTBTE_E_INVALID_ARG;
+    if (inst < 0 || inst >= (int)ctx->inst.size() || !off || (a && (!b || !W)))
+        return fail(ctx, RTBTE_E_INVALID_ARG, "bad download arguments");
+    InstHost &I = ctx->inst[inst];
+    if (!I.has_channels) return fail(ctx, RTBTE_E_STATE, "instance has no channels");
+    return ctx->precision == RTBTE_PREC_FP64
+               ? download_range<double>(ctx, I, which, seg_begin, seg_end, off, a, b, W, cap)
+               : download_range<float>(ctx, I, which, seg_begin, seg_end, off, a, b, W, cap);
 }
 
 int rtbte_set_stream(rtbte_ctx *ctx, void *stream) {

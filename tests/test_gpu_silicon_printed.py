@@ -63,3 +63,44 @@ def test_printed_silicon_sampled_rows_match_literal_sums(si80, state):
     for rows in (e_rows, m.n_c + p_rows, m.n_c + s_rows):
         assert np.linalg.norm(ref[rows]) > 0
         assert relL2(got[rows], ref[rows]) <= 1e-5
+
+
+def test_printed_silicon_sampled_lists_match_oracle(si80):
+    """Channel lists of sampled destinations of every family, read back segment by segment
+    (rtbte_download_segments), bit-exact in their indices against the oracle's brute-force
+    enumeration; weights within one FP32 ulp of the oracle's FP64 values."""
+    import paper_2412_13402_gb300 as rt
+
+    m, ctx, o = si80
+    rng = np.random.default_rng(6)
+
+    def w_close(got, want):
+        assert np.all(np.abs(got - want) <= 2.0 ** -23 * np.abs(want))
+
+    dests = np.sort(rng.choice(m.n_c, 6, replace=False)).astype(np.int32)
+    Lo = o.eph_lists(dests=dests)
+    for i, d in enumerate(dests):
+        for nu in range(m.nmodes):
+            g0 = (nu * m.n_c + int(d)) * 2
+            got = ctx.download_segments(0, rt.RTBTE_EPH, g0, g0 + 2)
+            for proc in (0, 1):
+                sl = slice(Lo["off"][2 * i + proc], Lo["off"][2 * i + proc + 1])
+                sel = (Lo["ph"][sl] // m.N_q) == nu
+                gs = slice(got["off"][proc], got["off"][proc + 1])
+                assert np.array_equal(got["a"][gs], Lo["src"][sl][sel])
+                assert np.array_equal(got["b"][gs], Lo["ph"][sl][sel])
+                w_close(got["W"][gs], Lo["W"][sl][sel])
+    phon = np.sort(rng.choice(m.n_ph, 6, replace=False))
+    Lp = o.phe_lists(phonons=phon)
+    for i, p in enumerate(phon):
+        got = ctx.download_segments(0, rt.RTBTE_PHE, int(p), int(p) + 1)
+        ls = slice(Lp["off"][i], Lp["off"][i + 1])
+        assert np.array_equal(got["a"], Lp["dst"][ls]) and np.array_equal(got["b"], Lp["src"][ls])
+        w_close(got["W"], Lp["W"][ls])
+    pd = np.sort(rng.choice(m.n_pp, 4, replace=False))
+    Lq = o.pp_lists(dests=pd)
+    for i, a in enumerate(pd):
+        got = ctx.download_segments(0, rt.RTBTE_PHPH, 2 * int(a), 2 * int(a) + 2)
+        ls = slice(Lq["off"][2 * i], Lq["off"][2 * i + 2])
+        assert np.array_equal(got["a"], Lq["b"][ls]) and np.array_equal(got["b"], Lq["c"][ls])
+        w_close(got["W"], Lq["W"][ls])

@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--accuracy-only", action="store_true", help="print only the error-versus-cost sweep")
     ap.add_argument("--surrogate-only", action="store_true", help="print only the learned slow-stage study")
     ap.add_argument("--silicon-only", action="store_true", help="print only the silicon-like precision study")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="print only the FP64 oracle's CPU-baseline table on this host (no GPU work)")
     ap.add_argument("--graphene-long", action="store_true",
                     help="print only the graphene-like workload integrated to 100 ps (ERK and MRI, FP32)")
     ap.add_argument("--silicon-long", action="store_true",
@@ -143,6 +145,57 @@ def oracle_sample_rate(model, y, seed=0, ne=192, nphe=1536, npp=192):
               f"{npp} ph-ph sub-lattice rows of the 180x180 graphene-like workload, each family scaled to its "
               f"full row count; {t3 - t0:.1f} s wall")
     return 1.0 / per_rhs, oracle.threads(), sample, t3 - t0
+
+
+def cpu_table():
+    """The CPU-baseline table of the FP64 oracle on this host: full-RHS evaluations per second of
+    the toy model (config 1, list sums), the graphene-like workload (config 2) and the 64-instance
+    ensemble (config 4; sampled literal sums scaled to full row counts), with all threads and with
+    one; and config 1's protocol run (Bogacki-Shampine, rtol 1e-8, to 1 ps) in simulated ps/s."""
+    import numpy as np
+
+    import oracle
+    import rtbte_inputs as ri
+
+    oracle.build()
+    allc = oracle.threads()
+    rows = []
+    m1 = ri.toy2d()
+    o1 = oracle.Oracle(m1)
+    o1.build_lists()
+    y1 = m1.y0()
+    for nt in (allc, 1):
+        oracle.set_threads(nt)
+        n, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < 2.0:
+            o1.rhs(y1)
+            n += 1
+        rows.append({"config": 1, "threads": nt, "rhs_evals_per_s": n / (time.perf_counter() - t0),
+                     "how": "full RHS from the stored lists, repeated for 2 s"})
+    oracle.set_threads(allc)
+    t0 = time.perf_counter()
+    _, st = o1.erk(y1, 0.0, 1.0, method=oracle.BS32, rtol=1e-8, atol_c=1e-15, atol_ph=1e-15)
+    c1_run = {"config": 1, "threads": allc, "seconds": time.perf_counter() - t0, "steps": st["steps"],
+              "sim_ps_per_s": 1.0 / (time.perf_counter() - t0), "method": "BS3 rtol 1e-8, atol 1e-15, to 1 ps"}
+    m2 = ri.graphene()
+    y2 = m2.y0()
+    for nt, scale in ((allc, 1), (1, 8)):
+        oracle.set_threads(nt)
+        r, _, _, sec = oracle_sample_rate(m2, y2, ne=192 // scale, nphe=1536 // scale, npp=192 // scale)
+        rows.append({"config": 2, "threads": nt, "rhs_evals_per_s": r,
+                     "how": f"sampled literal sums scaled to full row counts ({sec:.1f} s sample)"})
+    ms = ri.ensemble()
+    for nt in (allc, 1):
+        oracle.set_threads(nt)
+        per_rhs, t0 = 0.0, time.perf_counter()
+        for i, m in enumerate(ms):
+            r, _, _, _ = oracle_sample_rate(m, m.y0(), seed=i, ne=16, nphe=64, npp=16)
+            per_rhs += 1.0 / r
+        rows.append({"config": 4, "threads": nt, "rhs_evals_per_s": 1.0 / per_rhs,
+                     "instance_rhs_evals_per_s": len(ms) / per_rhs,
+                     "how": f"each instance sampled and scaled, summed ({time.perf_counter() - t0:.1f} s)"})
+    oracle.set_threads(allc)
+    return {"host_threads": allc, "rhs": rows, "config1_run": c1_run}
 
 
 def run_reference(args):
@@ -947,6 +1000,9 @@ def main():
         import rtbte_inputs as ri
 
         print(json.dumps(accuracy_sweep(rt, ri, torch.device("cuda", 0))), flush=True)
+        return 0
+    if args.cpu_table:
+        print(json.dumps(cpu_table()), flush=True)
         return 0
     if args.graphene_long:
         import torch

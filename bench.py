@@ -70,24 +70,37 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: only standalone full-RHS evaluations (warm-up + steps), no JSON line")
     ap.add_argument("--grid", type=int, default=180, help="k/q grid side of the graphene-like workload (profiling)")
-    ap.add_argument("--workload", default="graphene", choices=["graphene", "silicon_printed"],
-                    help="workload of --profile: the graphene-like one at --grid, or config 3 at the printed grids")
+    ap.add_argument("--workload", default="graphene", choices=["graphene", "silicon_printed", "ensemble16"],
+                    help="workload of --profile: the graphene-like one at --grid, config 3 at the printed grids, "
+                         "or the first 16 instances of the ensemble")
     return ap.parse_args()
 
 
 def run_profile(args):
     """Standalone collision-kernel launches for ncu captures: `--warmup` then `--steps` full-RHS
     evaluations of the graphene-like workload at grid side `--grid`, or (`--workload
-    silicon_printed`) of the silicon-like workload at the printed 80^3 / 40^3 grids."""
+    silicon_printed`) of the silicon-like workload at the printed 80^3 / 40^3 grids, or
+    (`--workload ensemble16`) of the first 16 ensemble instances in one batched launch."""
     import torch
 
     import paper_2412_13402_gb300 as rt
     import rtbte_inputs as ri
 
-    m = ri.graphene(n=args.grid) if args.workload == "graphene" else ri.silicon_printed()
-    ctx = rt.Context(m, precision="fp32")
-    ctx.upload_channels()
-    y = torch.tensor(m.y0(), device="cuda")
+    import numpy as np
+
+    if args.workload == "ensemble16":
+        ms = ri.ensemble()[:16]
+        ctx = rt.Context(ms, precision="fp32")
+        for i in range(len(ms)):
+            ctx.upload_channels(i)
+        y = torch.tensor(np.concatenate([m.y0() for m in ms]), device="cuda")
+        name = "ensemble16"
+    else:
+        m = ri.graphene(n=args.grid) if args.workload == "graphene" else ri.silicon_printed()
+        ctx = rt.Context(m, precision="fp32")
+        ctx.upload_channels()
+        y = torch.tensor(m.y0(), device="cuda")
+        name = m.name
     yd = torch.empty_like(y)
     ctx.rhs(y, yd)
     w = ctx.autotune(rt.RTBTE_ALL)
@@ -98,8 +111,9 @@ def run_profile(args):
     for _ in range(args.steps):
         ctx.rhs(y, yd)
     ms, n = ctx.kernel_time()
-    s = ctx.sizes(0)
-    print(f"profile workload={m.name} entries={s['eph_entries'] + s['phe_entries'] + s['pp_entries']} "
+    ent = sum(ctx.sizes(i)["eph_entries"] + ctx.sizes(i)["phe_entries"] + ctx.sizes(i)["pp_entries"]
+              for i in range(len(ctx.models)))
+    print(f"profile workload={name} entries={ent} "
           f"tuning={ctx.tuning()} rhs_kernel_avg_ms={ms / max(n, 1):.4f}", flush=True)
     ctx.close()
     return 0

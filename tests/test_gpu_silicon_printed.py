@@ -104,3 +104,31 @@ def test_printed_silicon_sampled_lists_match_oracle(si80):
         ls = slice(Lq["off"][2 * i], Lq["off"][2 * i + 2])
         assert np.array_equal(got["a"], Lq["b"][ls]) and np.array_equal(got["b"], Lq["c"][ls])
         w_close(got["W"], Lq["W"][ls])
+
+
+def test_printed_silicon_fp64_reads_populations_from_global_memory(oracle_lib):
+    """FP64 at the printed grids: f alone (290 KB) exceeds shared memory, so no q-blocking
+    helps and the collision kernel reads every population from global memory (the kernel
+    instance no smaller workload takes).  Sampled rows of every family within the FP64 parity
+    tolerance (1e-12) of the oracle's literal sums."""
+    import paper_2412_13402_gb300 as rt
+
+    m = ri.silicon_printed()
+    ctx = rt.Context(m, precision="fp64")
+    ctx.upload_channels()
+    assert ctx.sizes(0)["eph_q_blocks"] == 1
+    o = oracle_lib.Oracle(m)
+    rng = np.random.default_rng(12)
+    y = np.concatenate(ri.random_populations(m, 13))
+    full = o.pp_full_index()
+    e_rows = rng.choice(m.n_c, 8, replace=False)
+    p_rows = np.unique(np.concatenate([rng.choice(m.n_ph, 8, replace=False), full[rng.choice(len(full), 8, replace=False)]]))
+    em = np.zeros(m.n_c, np.uint8)
+    pm = np.zeros(m.n_ph, np.uint8)
+    em[e_rows] = 1
+    pm[p_rows] = 1
+    ref = o.rhs_literal(y, emask=em, pmask=pm)
+    got = ctx.rhs(torch.tensor(y, device="cuda")).cpu().numpy()
+    assert relL2(got[e_rows], ref[e_rows]) <= 1e-12
+    assert relL2(got[m.n_c + p_rows], ref[m.n_c + p_rows]) <= 1e-12
+    ctx.close()

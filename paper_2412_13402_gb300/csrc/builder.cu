@@ -7,8 +7,12 @@
 // involved is below the frequency cutoff, and writes the kept entries in order using
 // warp ballots (no sort pass).  The filter uses only IEEE FP64 subtraction/addition and
 // comparisons on the host-supplied energy tables, and this file is compiled without FMA
-// contraction, so the kept set and its order are bit-identical to any IEEE implementation
-// of the same rule.
+// contraction, so the kept set and its enumeration order are bit-identical to any IEEE
+// implementation of the same rule.  Two storage choices follow: the e-ph lists of a mode may
+// be split into phonon-wavevector blocks (segments (mode, block, electron, process)) so that
+// the populations a block reads fit in shared memory, and each full 128-entry block of a
+// segment is then reordered for shared-memory banks (bank_order); downloads return every
+// segment in enumeration order.
 //
 //   e-ph  (Eq. e-ph, first integral) destination d = (n, k), source s = (m, k'), mode nu,
 //         q = T(k' - k).  Emission keeps |(eps_d - hw) - eps_s| <= 3 sigma; absorption

@@ -4,8 +4,9 @@
 // stored channel entries are streamed from HBM exactly once per evaluation (16-byte
 // cache-streaming loads, 4 entries per lane), while the populations they gather are
 // staged per CTA in shared memory: the instance's electron occupations f plus, for e-ph
-// work, the occupations N of one phonon mode (the e-ph lists are blocked by mode for this
-// reason); for ph-e work only f; for ph-ph work the sub-lattice N.  A work item is a piece
+// work, the occupations N of one phonon mode, or of one wavevector block of it where the
+// whole mode does not fit (the e-ph lists are blocked by mode and block for this reason); for
+// ph-e work only f; for ph-ph work the sub-lattice N.  A work item is a piece
 // of a single destination segment; groups of long segments give each warp one item of up to
 // 512 entries, groups of short ones give each sub-warp of 8 or 16 lanes one item of up to 128
 // or 256 entries.  Lanes accumulate their entries with

@@ -321,6 +321,39 @@ def ladder(n: int = 6, quantum: float = 2.0 ** -5, T: float = 300.0, mu: float =
     )
 
 
+def ladder3d(n: int = 8, quantum: float = 2.0 ** -5, T: float = 300.0, mu: float = 0.0,
+             seed: int = 17, pp_stride: int = 1, with_pp: bool = True) -> Model:
+    """Exact-resonance test model on a folded 3D grid: electrons on an n^3 k-grid, phonons on
+    the (n/2)^3 q-grid (fold 2, so N_k = 8 N_q), electron energies (|dx| + |dy| + |dz| + 3 b)
+    quanta from the min-image grid displacement, dispersionless phonon branches at 1, 2 and
+    3 quanta, sigma = quantum/4.  Every kept channel is exactly resonant (a power-of-two
+    quantum makes every energy difference exact in binary floating point), so populations of
+    one temperature give a vanishing RHS and the total energy is conserved exactly for any
+    populations -- on a grid where the e-ph (1/N_q) and ph-e (1/N_k) normalisations differ."""
+    assert n % 2 == 0
+    nk = (n, n, n)
+    nq = (n // 2,) * 3
+
+    def eps_fn(b, cc):
+        d = sum(np.abs(_min_image(cc[:, ax], n)) for ax in range(3))
+        return (d + 3 * b).astype(np.float64) * quantum
+
+    e_band, e_k, e_eps = _electron_states(nk, 2, eps_fn, lambda b, e: np.ones(e.shape, bool))
+    Nq = int(np.prod(nq))
+    omega = np.concatenate([np.full(Nq, 1 * quantum), np.full(Nq, 2 * quantum), np.full(Nq, 3 * quantum)])
+    f0 = fermi_dirac(e_eps, mu, T)
+    N0 = bose_einstein(omega, T)
+    return Model(
+        name=f"ladder3d_{n}_f2", dim=3, nk=nk, nq=nq, fold=2, nbands=2,
+        e_band=e_band, e_k=e_k, e_eps=e_eps, nmodes=3, ph_omega=omega,
+        pp_stride=pp_stride if with_pp else 0,
+        sigma_eph=quantum / 4, sigma_pp=quantum / 4, omega_cut=0.001,
+        g2_seed=seed, v3_seed=seed + 1000003, g2_coef=np.array([1e-3, 2e-3, 0.5e-3]),
+        v3_coef=1e-5, lut_bits=8, lut=lognormal_lut(8, 1.0), f0=f0, N0=N0,
+        note="exact-resonance detailed-balance model, folded 3D grid (N_k != N_q)",
+    )
+
+
 def tiny(n=(4, 4, 1), nbands: int = 2, nmodes: int = 3, fold: int = 1, pp_stride: int = 1,
          seed: int = 99, sigma_eph: float = 0.05, sigma_pp: float = 0.02,
          rng_seed: int = 5) -> Model:
@@ -452,5 +485,5 @@ def random_populations(model: Model, seed: int, spread: float = 1.0):
 
 def by_name(name: str, **kw) -> Model:
     table = {"toy2d": toy2d, "graphene": graphene, "graphene_small": graphene_small,
-             "ladder": ladder, "tiny": tiny, "silicon": silicon, "silicon_printed": silicon_printed}
+             "ladder": ladder, "ladder3d": ladder3d, "tiny": tiny, "silicon": silicon, "silicon_printed": silicon_printed}
     return table[name](**kw)

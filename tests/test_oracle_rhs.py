@@ -150,6 +150,44 @@ def test_energy_conservation_exact_resonance(oracle_lib):
     assert abs(np.dot(w, rp)) < 1e-12 * np.dot(w, np.abs(rp))
 
 
+@pytest.mark.parametrize("T,mu", [(300.0, 0.0), (150.0, 0.04)])
+def test_detailed_balance_exact_resonance_folded_3d(oracle_lib, T, mu):
+    """Detailed balance on the folded 3D exact-resonance model (fold 2, N_k = 8 N_q): at
+    Fermi-Dirac / Bose-Einstein populations of one temperature every rate vanishes, from the
+    stored lists and from the literal sums."""
+    m = ri.ladder3d(n=8, T=T, mu=mu)
+    assert m.N_k == 8 * m.N_q
+    o = oracle_lib.Oracle(m)
+    o.build_lists()
+    ref = np.abs(o.rhs(symmetric_state(m, 3))).max()
+    assert ref > 1e-3
+    for rhs in (o.rhs(m.y0()), o.rhs_literal(m.y0())):
+        assert np.abs(rhs).max() < 1e-12 * ref
+
+
+def test_energy_conservation_exact_resonance_folded_3d(oracle_lib):
+    """Energy conservation of the e-ph + ph-e pair on a grid where N_k != N_q (fold 2 in 3D,
+    N_k = 8 N_q): d/dt [(2/N_k) sum eps f + (1/N_q) sum hw N] = 0 for arbitrary (inversion
+    symmetric) populations.  Each process moves hw from the electrons to one phonon, so this
+    holds only with the e-ph weight (2 pi/hbar)(1/N_q) and the ph-e weight (4 pi/hbar)(1/N_k)
+    of Eq. e-ph: exchanging N_k and N_q in either prefactor scales that side's rates by 8 and
+    breaks the balance (checked below on the oracle's own rows, rescaled as such a swap would)."""
+    m = ri.ladder3d(n=8)
+    o = oracle_lib.Oracle(m)
+    o.build_lists(oracle_lib.FAST)
+    y = symmetric_state(m, 5)
+    eps, w = m.e_eps, m.ph_omega
+    for r in (o.rhs(y, oracle_lib.FAST), o.rhs_literal(y, oracle_lib.FAST)):
+        e_el = (2.0 / m.N_k) * np.dot(eps, r[: m.n_c])
+        e_ph = (1.0 / m.N_q) * np.dot(w, r[m.n_c:])
+        assert abs(e_el) > 1e-6
+        assert abs(e_el + e_ph) < 1e-12 * abs(e_el)
+        # a swapped N_k <-> N_q in the ph-e weight (x N_k/N_q) or in the e-ph weight (x N_q/N_k)
+        ratio = m.N_k / m.N_q
+        assert abs(e_el + ratio * e_ph) > 1.0 * abs(e_el)
+        assert abs(e_el / ratio + e_ph) > 0.5 * abs(e_el)
+
+
 def test_energy_balance_equals_detuning_sum(oracle_lib):
     """Off resonance the e-ph energy change is the detuning-weighted rate sum:
     d/dt E = -(2/N_k) sum_{emission entries} W F_em (eps_d - hw - eps_s), exactly (to rounding)."""

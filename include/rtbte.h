@@ -116,6 +116,16 @@ typedef struct rtbte_desc {
                              fewest equal blocks that fit); prebuilt lists always use 1.
                              Segment order of built e-ph lists: (mode, block, electron,
                              process), sources ascending within a segment               */
+    /* Row slice (the destination-row split of one instance over several processes or GPUs;
+     * the sums over k and q of Eq. e-ph and Eq. ph-ph are independent per destination row).
+     * Single-instance contexts only: with row_end > row_begin the context evaluates only the
+     * state rows [row_begin, row_end) of y (electron rows 0..n_c-1 first, then phonon rows
+     * n_c + p): channel lists are stored for those destinations alone, rtbte_rhs writes 0 on
+     * every other row, and each owned row gets the same bits as in an unsliced context (the
+     * builder counts every row so that the work items are cut alike).  The caller gathers the
+     * slices (e.g. an all-gather, or a sum all-reduce since other rows are 0).
+     * rtbte_advance_to refuses a sliced context (STATE).  0, 0: every row. */
+    int64_t row_begin, row_end;
 } rtbte_desc;
 
 /* Channel source for rtbte_upload_channels.
@@ -132,6 +142,9 @@ typedef struct rtbte_desc {
  *   Weights are FP64 on input and stored in the context precision. */
 #define RTBTE_CH_BUILD 0
 #define RTBTE_CH_PREBUILT 1
+#define RTBTE_CH_COUNT 2 /* count every row's channels on the device without storing them (for
+                            rtbte_row_entries, e.g. to balance row slices); the instance still has
+                            no channels afterwards */
 typedef struct rtbte_channels {
     int32_t mode;
     int32_t reserved;
@@ -266,8 +279,10 @@ int rtbte_set_controller(rtbte_ctx *ctx, int inst, const rtbte_controller *in);
  * on the context's stream.  Errors: INVALID_ARG, STATE (no channels), CUDA. */
 int rtbte_phph_rates(rtbte_ctx *ctx, const double *y, double *rates);
 
-/* Advance the device state y (FP64 [n_y_total], caller-owned) from opt->t0 to t_out with
- * the method of `opt`.  All stepping, error norms and step-size control run on the device:
+/* Advance the state y (FP64 [n_y_total], caller-owned) from opt->t0 to t_out with the method
+ * of `opt`.  y is a device pointer, or a host pointer (pinned memory copies fastest), which
+ * the call stages through a context buffer: copied to the device first and the result copied
+ * back before it returns.  All stepping, error norms and step-size control run on the device:
  * each integration span is one launch of a CUDA graph whose WHILE node repeats the attempt
  * kernels until every instance is done (at most opt->chunk attempts per launch), and the host
  * reads the status block once per launch (MRI_ADAPT: the host also reads the slow error
@@ -279,6 +294,13 @@ int rtbte_advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ 
 
 /* Sizes of instance `inst` (channel counts are 0 before rtbte_upload_channels). */
 int rtbte_get_sizes(const rtbte_ctx *ctx, int inst, rtbte_sizes *out);
+
+/* Logical channel entries per state row of instance `inst` (host int64 [n_c + n_ph]: an
+ * electron row counts its e-ph entries, a phonon row its ph-e and ph-ph entries), after
+ * rtbte_upload_channels in any mode (RTBTE_CH_COUNT included); rows outside a context's row
+ * slice count 0 unless the mode was RTBTE_CH_COUNT.  The cost weights for balancing row
+ * slices.  Errors: INVALID_ARG, STATE (nothing counted yet). */
+int rtbte_row_entries(const rtbte_ctx *ctx, int inst, int64_t *counts);
 
 /* Copy instance `inst`'s stored lists back to host in the PREBUILT logical order (padding
  * removed; q-blocked e-ph lists are merged back into segments (mode, electron, process) with
@@ -336,11 +358,11 @@ const char *rtbte_status_string(int status);
 
 /* ---- allocation-free e-ph RHS ----------------------------------------------------------
  * The paper has no counterpart to this entry point.  It exists for callers that cannot
- * allocate device memory: code running while a CUDA graph is being captured (cudaMalloc is
- * not allowed there, or is not recorded into the graph), programs whose device memory is
- * owned by another allocator or a pre-reserved arena, and latency-critical loops where an
- * allocation's implicit synchronisation is not acceptable.  It needs no context and calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * allocate device memory: programs whose device memory is owned entirely by another
+ * allocator or by an arena reserved at start-up (a serving runtime, a host application that
+ * budgets every byte of the GPU), and latency-critical loops where an allocation's implicit
+ * synchronisation is not acceptable.  It needs no context and calls no cudaMalloc, cudaFree
+ * or other allocating routine.
  *
  * Writes ydot[0..n_c) = I^{e-ph} (the electron rows of one instance) from caller-owned
  * device arrays: y (FP64 [n_c + n_ph], the instance's state vector) and the e-ph channel

@@ -28,12 +28,12 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error"
 RTBTE_EPH, RTBTE_PHE, RTBTE_PHPH = 1, 2, 4
 RTBTE_FAST, RTBTE_SLOW, RTBTE_ALL = 3, 4, 7
 RTBTE_PREC_FP32_COMP, RTBTE_PREC_FP64 = 0, 1
-RTBTE_CH_BUILD, RTBTE_CH_PREBUILT = 0, 1
+RTBTE_CH_BUILD, RTBTE_CH_PREBUILT, RTBTE_CH_COUNT = 0, 1, 2
 RTBTE_RK4, RTBTE_BS32, RTBTE_ZON43, RTBTE_MRI_KW3, RTBTE_SPLIT_RK4, RTBTE_MRI_ADAPT = 0, 1, 2, 3, 4, 5
 HBAR_EV_PS = 6.582119569e-4
 
 EXPORTS = ["rtbte_desc_defaults", "rtbte_integ_defaults", "rtbte_create", "rtbte_upload_channels", "rtbte_rhs",
-           "rtbte_advance_to", "rtbte_get_controller", "rtbte_set_controller", "rtbte_phph_rates", "rtbte_get_sizes", "rtbte_download_channels", "rtbte_download_segments", "rtbte_set_stream",
+           "rtbte_advance_to", "rtbte_get_controller", "rtbte_set_controller", "rtbte_phph_rates", "rtbte_get_sizes", "rtbte_row_entries", "rtbte_download_channels", "rtbte_download_segments", "rtbte_set_stream",
            "rtbte_autotune", "rtbte_get_tuning", "rtbte_set_graph_mode", "rtbte_set_kernel_timing", "rtbte_kernel_time", "rtbte_launch_count", "rtbte_last_error",
            "rtbte_status_string", "rtbte_eph_rhs_noalloc", "rtbte_surrogate_create", "rtbte_surrogate_collect",
            "rtbte_surrogate_train", "rtbte_surrogate_predict", "rtbte_surrogate_loss_grad",
@@ -53,7 +53,8 @@ class InstanceDesc(C.Structure):
 
 class Desc(C.Structure):
     _fields_ = [("n_instances", C.c_int32), ("precision", C.c_int32), ("inst", C.c_void_p), ("hbar", C.c_double),
-                ("stream", C.c_void_p), ("device", C.c_int32), ("eph_q_blocks", C.c_int32)]
+                ("stream", C.c_void_p), ("device", C.c_int32), ("eph_q_blocks", C.c_int32),
+                ("row_begin", C.c_int64), ("row_end", C.c_int64)]
 
 
 class Channels(C.Structure):
@@ -130,6 +131,7 @@ def load():
         L.rtbte_get_controller.argtypes = [vp, i32, vp]
         L.rtbte_set_controller.argtypes = [vp, i32, vp]
         L.rtbte_get_sizes.argtypes = [vp, i32, vp]
+        L.rtbte_row_entries.argtypes = [vp, i32, vp]
         L.rtbte_download_channels.argtypes = [vp, i32, C.c_uint, vp, vp, vp, vp]
         L.rtbte_download_segments.argtypes = [vp, i32, C.c_uint, i64, i64, vp, vp, vp, vp, i64]
         L.rtbte_set_stream.argtypes = [vp, vp]
@@ -238,7 +240,7 @@ class Context:
     """One library context over one or more independent instances sharing a state vector."""
 
     def __init__(self, models, precision: str = "fp32", stream=None, device: int = 0, hbar: float = HBAR_EV_PS,
-                 eph_q_blocks: int = 0):
+                 eph_q_blocks: int = 0, row_range: tuple | None = None):
         import torch
 
         if not torch.cuda.is_available():
@@ -261,15 +263,21 @@ class Context:
         d.stream = self.stream.cuda_stream
         d.device = device
         d.eph_q_blocks = eph_q_blocks
+        if row_range is not None:  # evaluate only the state rows [begin, end) (see rtbte_desc)
+            d.row_begin, d.row_end = int(row_range[0]), int(row_range[1])
+        self.row_range = row_range
         self.device = device
         self.ctx = rtbte_create(d)
 
     # ---- setup --------------------------------------------------------------------
-    def upload_channels(self, inst: int = 0, prebuilt: dict | None = None):
+    def upload_channels(self, inst: int = 0, prebuilt: dict | None = None, count_only: bool = False):
         """Build the channel lists on the device, or copy `prebuilt` host lists (dict with
-        keys eph/phe/pp as produced by the oracle's list builders, FP64 weights)."""
+        keys eph/phe/pp as produced by the oracle's list builders, FP64 weights), or with
+        count_only only count every row's channels (for row_entries)."""
         ch = Channels()
-        if prebuilt is None:
+        if count_only:
+            ch.mode = RTBTE_CH_COUNT
+        elif prebuilt is None:
             ch.mode = RTBTE_CH_BUILD
         else:
             ch.mode = RTBTE_CH_PREBUILT
@@ -297,6 +305,13 @@ class Context:
         s = Sizes()
         _check(self.ctx, load().rtbte_get_sizes(self.ctx, inst, C.addressof(s)))
         return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def row_entries(self, inst: int = 0) -> np.ndarray:
+        """Logical channel entries per state row (the cost weights of row slices)."""
+        m = self.models[inst]
+        out = np.zeros(m.n_c + m.n_ph, np.int64)
+        _check(self.ctx, load().rtbte_row_entries(self.ctx, inst, _p(out)))
+        return out
 
     def download_channels(self, inst: int, which: int) -> dict:
         s = self.sizes(inst)
@@ -340,12 +355,14 @@ class Context:
         return ydot
 
     def advance_to(self, t_out: float, y, options: "Integ | None" = None, stats: "Stats | None" = None, **opts):
-        """Integrate the device state y to t_out.  With keyword options: returns a dict of the
-        statistics.  With a prebuilt `options` (integ_options(...)) and a reusable `stats`
-        object: fills and returns `stats` (no per-call allocation, for tight driver loops)."""
+        """Integrate the state y (FP64 torch tensor on the device, or in host memory -- pinned
+        copies fastest -- which the library stages in and out) to t_out.  With keyword options:
+        returns a dict of the statistics.  With a prebuilt `options` (integ_options(...)) and a
+        reusable `stats` object: fills and returns `stats` (no per-call allocation, for tight
+        driver loops)."""
         import torch
 
-        assert y.is_cuda and y.dtype == torch.float64 and y.is_contiguous()
+        assert y.dtype == torch.float64 and y.is_contiguous()
         if options is not None:
             st = stats if stats is not None else Stats()
             rtbte_advance_to(self.ctx, t_out, y.data_ptr(), options, st)

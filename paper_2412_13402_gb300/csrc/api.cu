@@ -127,15 +127,20 @@ int setup_instance(rtbte_ctx *ctx, const rtbte_instance_desc &d, InstHost &I) {
 template <class R>
 int upload_prebuilt(rtbte_ctx *ctx, InstHost &I, const rtbte_channels *ch) {
     const int nc = I.d.n_c, nm = I.d.nmodes;
-    auto pack = [&](long long nseg, const int64_t *off, auto encode, std::vector<long long> &cnt,
-                    std::vector<long long> &poff, DevBuf &didx, DevBuf &dW, const double *W) -> int {
+    // row_of(g): state row of segment g; segments outside the row slice are stored empty
+    auto pack = [&](long long nseg, const int64_t *off, auto encode, auto row_of, std::vector<long long> &cnt,
+                    std::vector<long long> &plen, std::vector<long long> &poff, DevBuf &didx, DevBuf &dW,
+                    const double *W) -> int {
         cnt.assign(nseg, 0);
+        plen.assign(nseg, 0);
         poff.assign(nseg + 1, 0);
         for (long long g = 0; g < nseg; ++g) {
             long long c = off[g + 1] - off[g];
             if (c < 0) return fail(ctx, RTBTE_E_INVALID_ARG, "offsets must be non-decreasing");
-            cnt[g] = c;
-            poff[g + 1] = poff[g] + round_up(c, kSegPad);
+            plen[g] = round_up(c, kSegPad);
+            const long long r = row_of(g);
+            cnt[g] = (r >= I.row_lo && r < I.row_hi) ? c : 0;
+            poff[g + 1] = poff[g] + round_up(cnt[g], kSegPad);
         }
         const long long E = poff[nseg];
         std::vector<uint32_t> hidx(std::max<long long>(E, 4), 0u);
@@ -170,7 +175,8 @@ int upload_prebuilt(rtbte_ctx *ctx, InstHost &I, const rtbte_channels *ch) {
                   *code = (uint32_t)s | ((uint32_t)q << I.s_bits);
                   return true;
               },
-              I.eph_cnt, I.eph_off, I.eph_idx, I.eph_W, ch->eph_W);
+              [&](long long g) { return (g / 2) % nc; }, I.eph_cnt, I.eph_plen, I.eph_off, I.eph_idx, I.eph_W,
+              ch->eph_W);
     if (rc) return rc;
     rc = pack(I.n_ph, ch->phe_off,
               [&](long long, long long e, uint32_t *code) {
@@ -179,7 +185,8 @@ int upload_prebuilt(rtbte_ctx *ctx, InstHost &I, const rtbte_channels *ch) {
                   *code = (uint32_t)d | ((uint32_t)s << I.s_bits);
                   return true;
               },
-              I.phe_cnt, I.phe_off, I.phe_idx, I.phe_W, ch->phe_W);
+              [&](long long g) { return (long long)nc + g; }, I.phe_cnt, I.phe_plen, I.phe_off, I.phe_idx, I.phe_W,
+              ch->phe_W);
     if (rc) return rc;
     I.pp_cnt.clear();
     I.pp_off.assign(1, 0);
@@ -195,10 +202,12 @@ int upload_prebuilt(rtbte_ctx *ctx, InstHost &I, const rtbte_channels *ch) {
                       *code = (uint32_t)b | ((uint32_t)c << I.pp_bits);
                       return true;
                   },
-                  I.pp_cnt, I.pp_off, I.pp_idx, I.pp_W, ch->pp_W);
+                  [&](long long g) { return (long long)nc + (long long)I.pp_full[g / 2]; }, I.pp_cnt, I.pp_plen,
+                  I.pp_off, I.pp_idx, I.pp_W, ch->pp_W);
         if (rc) return rc;
     }
     I.has_channels = true;
+    I.counted = true;
     return RTBTE_OK;
 }
 
@@ -448,6 +457,18 @@ int rtbte_create(const rtbte_desc *d, rtbte_ctx **out) {
         P += I.M_pad;
     }
     ctx->n_y = y;
+    if (d->row_end > d->row_begin || d->row_begin != 0 || d->row_end != 0) {  // a row slice
+        if (d->n_instances != 1 || d->row_begin < 0 || d->row_end <= d->row_begin || d->row_end > y)
+            return bail(fail(ctx, RTBTE_E_INVALID_ARG, "row slice must lie in [0, n_y) of a single-instance context"));
+        ctx->inst[0].row_lo = d->row_begin;
+        ctx->inst[0].row_hi = d->row_end;
+        ctx->sliced = true;
+    } else {
+        for (auto &I : ctx->inst) {
+            I.row_lo = 0;
+            I.row_hi = I.d.n_c + I.n_ph;
+        }
+    }
     ctx->popf_len = f;
     ctx->popN_len = N;
     ctx->popP_len = P;
@@ -479,8 +500,10 @@ int rtbte_upload_channels(rtbte_ctx *ctx, int inst, const rtbte_channels *ch) {
     InstHost &I = ctx->inst[inst];
     ctx->plan_valid = false;
     I.has_channels = false;
+    I.counted = false;
     destroy_graphs(ctx);  // graphs capture the plan's pointers
-    if (ch->mode == RTBTE_CH_BUILD) return build_channels(ctx, inst);
+    if (ch->mode == RTBTE_CH_BUILD) return build_channels(ctx, inst, false);
+    if (ch->mode == RTBTE_CH_COUNT) return build_channels(ctx, inst, true);
     if (ch->mode == RTBTE_CH_PREBUILT)
         return ctx->precision == RTBTE_PREC_FP64 ? upload_prebuilt<double>(ctx, I, ch) : upload_prebuilt<float>(ctx, I, ch);
     return fail(ctx, RTBTE_E_INVALID_ARG, "unknown channel mode");
@@ -555,10 +578,21 @@ int rtbte_advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ 
     Range nvtx_range("rtbte_advance_to");
     if (!ctx) return RTBTE_E_INVALID_ARG;
     if (!y || !opt) return fail(ctx, RTBTE_E_INVALID_ARG, "bad advance_to arguments");
-    if (!ptr_is_device(y)) return fail(ctx, RTBTE_E_INVALID_ARG, "y must be a device pointer");
+    if (ctx->sliced)
+        return fail(ctx, RTBTE_E_STATE, "a row-sliced context evaluates its rows only; integrate the gathered RHS");
     int rc;
     if ((rc = ensure_plan(ctx))) return rc;
-    return advance_to(ctx, t_out, y, opt, st);
+    if (ptr_is_device(y)) return advance_to(ctx, t_out, y, opt, st);
+    // host state: staged through a context buffer (copy in, integrate, copy the result back)
+    const size_t nb = sizeof(double) * ctx->n_y;
+    if (!ctx->ystage.p && (rc = dev_alloc(ctx, ctx->ystage, nb, false))) return rc;
+    RT_CUDA(ctx, cudaMemcpyAsync(ctx->ystage.p, y, nb, cudaMemcpyHostToDevice, ctx->stream));
+    const int status = advance_to(ctx, t_out, ctx->ystage.as<double>(), opt, st);
+    if (status == RTBTE_E_CUDA || status == RTBTE_E_INVALID_ARG || status == RTBTE_E_OOM || status == RTBTE_E_STATE)
+        return status;  // y untouched
+    RT_CUDA(ctx, cudaMemcpyAsync(y, ctx->ystage.p, nb, cudaMemcpyDeviceToHost, ctx->stream));
+    RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return status;
 }
 
 int rtbte_get_sizes(const rtbte_ctx *ctx, int inst, rtbte_sizes *out) {
@@ -585,6 +619,18 @@ int rtbte_get_sizes(const rtbte_ctx *ctx, int inst, rtbte_sizes *out) {
     const long long es = 4 + (long long)ctx->real_size;
     out->channel_bytes = es * (out->eph_stored + out->phe_stored + out->pp_stored);
     out->eph_q_blocks = I.has_channels ? I.eph_nqb : 0;
+    return RTBTE_OK;
+}
+
+int rtbte_row_entries(const rtbte_ctx *ctx, int inst, int64_t *counts) {
+    if (!ctx || !counts || inst < 0 || inst >= (int)ctx->inst.size()) return RTBTE_E_INVALID_ARG;
+    const InstHost &I = ctx->inst[inst];
+    if (!I.counted) return RTBTE_E_STATE;
+    const long long nc = I.d.n_c;
+    std::fill(counts, counts + nc + I.n_ph, (int64_t)0);
+    for (size_t g = 0; g < I.eph_cnt.size(); ++g) counts[(g / 2) % nc] += I.eph_cnt[g];  // (mode, block, d, proc)
+    for (size_t p = 0; p < I.phe_cnt.size(); ++p) counts[nc + p] += I.phe_cnt[p];
+    for (size_t g = 0; g < I.pp_cnt.size(); ++g) counts[nc + I.pp_full[g / 2]] += I.pp_cnt[g];
     return RTBTE_OK;
 }
 

@@ -115,6 +115,7 @@ __global__ void eph_enum(BuildTables T, long long *counts, const long long *off,
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     if (warp >= T.n_c) return;
     const int d = (int)warp;
+    if (FILL && (d < T.row_lo || d >= T.row_hi)) return;  // row outside the slice: nothing stored
     const int4 kd = T.ek[d];
     const double ed = T.eps[d];
     const unsigned lt = (1u << lane) - 1u;
@@ -188,6 +189,7 @@ __global__ void phe_enum(BuildTables T, long long *counts, const long long *off,
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     if (warp >= T.N_ph) return;
     const long long p = warp;
+    if (FILL && (T.n_c + p < T.row_lo || T.n_c + p >= T.row_hi)) return;  // row outside the slice
     const int nu = (int)(p / T.N_q);
     const int ql = (int)(p - (long long)nu * T.N_q);
     const double w = T.omega[p];
@@ -268,6 +270,7 @@ __global__ void pp_enum(BuildTables T, long long *counts, const long long *off, 
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     if (warp >= T.M) return;
     const int a = (int)warp;
+    if (FILL && (T.n_c + T.pp_full[a] < T.row_lo || T.n_c + T.pp_full[a] >= T.row_hi)) return;  // outside the slice
     const double wa = T.omega[T.pp_full[a]];
     const int ql = (int)(a % T.N_qs);
     const int qa0 = ql % T.nqs[0], qa1 = (ql / T.nqs[0]) % T.nqs[1], qa2 = ql / (T.nqs[0] * T.nqs[1]);
@@ -450,6 +453,8 @@ BuildTables tables_of(rtbte_ctx *ctx, InstHost &I) {
     T.pp_bits = I.pp_bits;
     T.eph_nqb = I.eph_nqb;
     T.eph_qblk = I.eph_qblk;
+    T.row_lo = I.row_lo;
+    T.row_hi = I.row_hi;
     T.sigma_eph = I.d.sigma_eph;
     T.sigma_pp = I.d.sigma_pp;
     T.cut_eph = 3.0 * I.d.sigma_eph;
@@ -482,8 +487,30 @@ void choose_q_blocks(rtbte_ctx *ctx, InstHost &I) {
     I.eph_qblk = (int)std::max<long long>(qblk, 4);
 }
 
+// Counts of every segment (all rows) -> padded lengths kept for the plan's lane choice; counts
+// of segments whose destination row lies outside the instance's row slice are then zeroed
+// (also on the device, where the bank-order pass reads them).  row_of(g) = state row of g.
+template <class RowOf>
+int slice_counts(rtbte_ctx *ctx, const InstHost &I, std::vector<long long> &cnt, std::vector<long long> &plen,
+                 DevBuf &dcnt, RowOf row_of) {
+    plen.resize(cnt.size());
+    bool cut = false;
+    for (size_t g = 0; g < cnt.size(); ++g) {
+        plen[g] = round_up(cnt[g], kSegPad);
+        const long long r = row_of((long long)g);
+        if (r < I.row_lo || r >= I.row_hi) {
+            cut = cut || cnt[g] != 0;
+            cnt[g] = 0;
+        }
+    }
+    if (cut && !cnt.empty())
+        RT_CUDA(ctx, cudaMemcpyAsync(dcnt.p, cnt.data(), sizeof(long long) * cnt.size(), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+    return RTBTE_OK;
+}
+
 template <class R>
-int run_build(rtbte_ctx *ctx, InstHost &I) {
+int run_build(rtbte_ctx *ctx, InstHost &I, bool count_only) {
     BuildTables T = tables_of(ctx, I);
     const int threads = 256, wpb = threads / 32;
     DevBuf cnt, off;
@@ -500,7 +527,17 @@ int run_build(rtbte_ctx *ctx, InstHost &I) {
     I.eph_cnt.assign(nseg, 0);
     RT_CUDA(ctx, cudaMemcpyAsync(I.eph_cnt.data(), cnt.p, sizeof(long long) * nseg, cudaMemcpyDeviceToHost, ctx->stream));
     RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    long long E = pad_offsets(I.eph_cnt, I.eph_off);
+    int rc;
+    const long long nc = I.d.n_c;
+    if (count_only) {
+        cnt.release();
+        I.eph_off.clear();
+    } else {
+        if ((rc = slice_counts(ctx, I, I.eph_cnt, I.eph_plen, cnt, [&](long long g) { return (g / 2) % nc; })))
+            return rc;
+    }
+    long long E = count_only ? 0 : pad_offsets(I.eph_cnt, I.eph_off);
+    if (!count_only) {
     I.eph_idx.release();
     I.eph_W.release();
     RT_CUDA(ctx, cudaMalloc(&I.eph_idx.p, sizeof(uint32_t) * std::max<long long>(E, 4)));
@@ -512,11 +549,11 @@ int run_build(rtbte_ctx *ctx, InstHost &I) {
         T, nullptr, off.as<long long>(), I.eph_idx.as<uint32_t>(), I.eph_W.p);
     RT_CUDA(ctx, cudaGetLastError());
     ctx->launches++;
-    int rc;
     if ((rc = order_banks<R>(ctx, I, PART_EPH, I.eph_idx, I.eph_W, off, cnt, nseg))) return rc;
     RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     cnt.release();
     off.release();
+    }
     // ---- ph-e
     long long nph = I.n_ph;
     RT_CUDA(ctx, cudaMalloc(&cnt.p, sizeof(long long) * std::max<long long>(nph, 1)));
@@ -527,6 +564,11 @@ int run_build(rtbte_ctx *ctx, InstHost &I) {
     I.phe_cnt.assign(nph, 0);
     RT_CUDA(ctx, cudaMemcpyAsync(I.phe_cnt.data(), cnt.p, sizeof(long long) * nph, cudaMemcpyDeviceToHost, ctx->stream));
     RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (count_only) {
+        cnt.release();
+        I.phe_off.clear();
+    } else {
+    if ((rc = slice_counts(ctx, I, I.phe_cnt, I.phe_plen, cnt, [&](long long g) { return nc + g; }))) return rc;
     E = pad_offsets(I.phe_cnt, I.phe_off);
     I.phe_idx.release();
     I.phe_W.release();
@@ -543,6 +585,7 @@ int run_build(rtbte_ctx *ctx, InstHost &I) {
     RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     cnt.release();
     off.release();
+    }
     // ---- ph-ph
     I.pp_cnt.clear();
     I.pp_off.assign(1, 0);
@@ -559,6 +602,14 @@ int run_build(rtbte_ctx *ctx, InstHost &I) {
         I.pp_cnt.assign(ns, 0);
         RT_CUDA(ctx, cudaMemcpyAsync(I.pp_cnt.data(), cnt.p, sizeof(long long) * ns, cudaMemcpyDeviceToHost, ctx->stream));
         RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (count_only) {
+            cnt.release();
+            I.pp_off.assign(1, 0);
+            return RTBTE_OK;
+        }
+        if ((rc = slice_counts(ctx, I, I.pp_cnt, I.pp_plen, cnt,
+                               [&](long long g) { return nc + (long long)I.pp_full[g / 2]; })))
+            return rc;
         E = pad_offsets(I.pp_cnt, I.pp_off);
         RT_CUDA(ctx, cudaMalloc(&I.pp_idx.p, sizeof(uint32_t) * std::max<long long>(E, 4)));
         RT_CUDA(ctx, cudaMalloc(&I.pp_W.p, sizeof(R) * std::max<long long>(E, 4)));
@@ -611,14 +662,20 @@ int upload_tables(rtbte_ctx *ctx, int i) {
     return RTBTE_OK;
 }
 
-int build_channels(rtbte_ctx *ctx, int i) {
+int build_channels(rtbte_ctx *ctx, int i, bool count_only) {
     InstHost &I = ctx->inst[i];
     if (I.d.nbands * kMaxPre * kMaxPre * kMaxPre > kMaxCand && I.d.fold > 1)
         return fail(ctx, RTBTE_E_UNSUPPORTED, "too many bands for the folded ph-e candidate buffer");
     if (I.d.nbands > kMaxCand) return fail(ctx, RTBTE_E_UNSUPPORTED, "too many bands");
-    int rc = ctx->precision == RTBTE_PREC_FP64 ? run_build<double>(ctx, I) : run_build<float>(ctx, I);
+    if (count_only) {  // nothing stored: the lists of an earlier upload go
+        DevBuf *bufs[] = {&I.eph_idx, &I.eph_W, &I.phe_idx, &I.phe_W, &I.pp_idx, &I.pp_W, &I.pp_off_dev};
+        for (DevBuf *b : bufs) b->release();
+    }
+    int rc = ctx->precision == RTBTE_PREC_FP64 ? run_build<double>(ctx, I, count_only)
+                                               : run_build<float>(ctx, I, count_only);
     if (rc) return rc;
-    I.has_channels = true;
+    I.counted = true;
+    I.has_channels = !count_only;
     return RTBTE_OK;
 }
 

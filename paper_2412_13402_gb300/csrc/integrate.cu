@@ -138,10 +138,9 @@ __global__ void __launch_bounds__(kRedThreads) stage_kernel(RowParams Q, StageAr
             const bool out = local < I.n_c ? (ynew < -a.cp.atol_c || ynew > 1.0 + a.cp.atol_c) : (ynew < -a.cp.atol_ph);
             if (out && a.range) atomicAdd(a.range + ii, 1ULL);
             double x2 = 0.0;
-            if (a.T.has_emb) {  // error weight in precision R (a relative 1e-7 in the norm is immaterial)
-                const double e = h * s2;
-                const R w = R(1) / ((R)a.cp.rtol * (R)fabs(y[c]) + (R)atol_of(a.cp, I, local));
-                const double x = (double)((R)e * w);
+            if (a.T.has_emb) {  // error weight and weighted error in FP64 (step acceptance reads them)
+                const double w = 1.0 / (a.cp.rtol * fabs(y[c]) + atol_of(a.cp, I, local));
+                const double x = h * s2 * w;
                 x2 = x * x;
             }
             if (!isfinite(ynew)) x2 = __longlong_as_double(0x7ff8000000000000LL);

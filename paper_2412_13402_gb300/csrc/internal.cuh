@@ -124,6 +124,20 @@ inline int bits_for(long long n) {  // bits needed for indices 0..n-1
 }
 inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 
+// The dynamic shared-memory limit is an attribute of the kernel function, shared by every
+// context (and surrogate) of the process: it is set to the device's opt-in maximum less the
+// kernel's static shared memory, so that no context lowers it below another's launches.
+inline cudaError_t allow_max_dynamic_smem(const void *f) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 // ---- device buffer ----------------------------------------------------------
 struct DevBuf {
     void *p = nullptr;
@@ -151,6 +165,7 @@ struct BuildTables {
     long long N_k, N_q, N_ph, M, N_qs;
     int s_bits, q_bits, pp_bits;
     int eph_nqb, eph_qblk;  // e-ph q-blocks per mode, q points per block
+    long long row_lo, row_hi;  // fill passes store only destinations whose state row is in [row_lo, row_hi)
     double cut_eph, cut_pp, sigma_eph, sigma_pp, omega_cut;
     double pref_eph, pref_phe, pref_pp;  // 2pi/(hbar N_q), 4pi/(hbar N_k), 36pi/(hbar N_q,pp)
     double v3;
@@ -173,8 +188,13 @@ struct InstHost {
     DevBuf eph_idx, eph_W, phe_idx, phe_W, pp_idx, pp_W;
     std::vector<long long> eph_off, phe_off, pp_off;  // padded CSR offsets (host copy)
     DevBuf pp_off_dev;                                // device copy of pp_off (made on first use)
-    std::vector<long long> eph_cnt, phe_cnt, pp_cnt;  // logical counts per segment
+    std::vector<long long> eph_cnt, phe_cnt, pp_cnt;  // logical counts per segment (0 outside the row slice)
+    // padded segment lengths over EVERY row (row slices included), from which the plan takes each
+    // staging group's lanes per item, so that a sliced context cuts its items like a full one
+    std::vector<long long> eph_plen, phe_plen, pp_plen;
+    long long row_lo = 0, row_hi = 0;  // state-row slice [row_lo, row_hi) of this instance (all rows: 0, n_y)
     bool has_channels = false;
+    bool counted = false;  // per-segment counts exist (after any upload mode, RTBTE_CH_COUNT included)
     long long y_off = 0, f_off = 0, N_off = 0, P_off = 0;
 };
 
@@ -217,6 +237,7 @@ struct rtbte_ctx {
     rtbte::DevBuf slow_save;          // tolerance-chosen MRI: y_n, the single-step result, error norms
     double h_slow = 0.0;              // tolerance-chosen MRI: slow step proposal after the last call
     int eph_q_blocks = 0;             // requested e-ph q-blocks (0: automatic)
+    bool sliced = false;              // the single instance evaluates a row slice only (rtbte_desc)
     std::map<long long, cudaGraphExec_t> graphs;
     std::map<long long, int> graph_launches;  // kernels per attempt of each attempt-loop graph
     bool use_graphs = true;                   // attempts through the device-loop graph (else direct launches)
@@ -237,7 +258,7 @@ struct rtbte_ctx {
 
 namespace rtbte {
 // builder.cu
-int build_channels(rtbte_ctx *ctx, int inst);
+int build_channels(rtbte_ctx *ctx, int inst, bool count_only);
 int upload_tables(rtbte_ctx *ctx, int inst);
 // rhs.cu
 int make_plan(rtbte_ctx *ctx);

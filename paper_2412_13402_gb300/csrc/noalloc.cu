@@ -1,13 +1,13 @@
 // noalloc.cu -- an e-ph RHS entry point that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being captured
-// (allocation is not allowed there, or is not recorded into the graph), programs whose
-// device memory is owned entirely by another allocator or a pre-reserved arena, and
-// latency-critical loops where an allocation's implicit device synchronisation is not
-// acceptable.  rtbte_eph_rhs_noalloc serves them: the caller passes every input and output
-// as device pointers, and the only working memory (single-precision copies of the
-// populations and one compensated partial sum per list segment) lives in the file-scope
-// array below, which every device that loads this library holds until the process exits.
+// Some callers cannot call cudaMalloc: programs whose device memory is owned entirely by
+// another allocator or by an arena reserved at start-up (a serving runtime, a host
+// application that budgets every byte of the GPU), and latency-critical loops where an
+// allocation's implicit device synchronisation is not acceptable.  rtbte_eph_rhs_noalloc
+// serves them: the caller passes every input and output as device pointers, and the only
+// working memory (single-precision copies of the populations and one compensated partial sum
+// per list segment) lives in the file-scope array below, which every device that loads this
+// library holds until the process exits.
 //
 // The arithmetic is that of the collision kernel in rhs.cu restricted to the electron rows
 // of the e-ph integral: FP32 gathers and products, per-lane two-sum accumulation, a

@@ -688,13 +688,14 @@ int make_plan(rtbte_ctx *ctx) {
     std::vector<int> eoff, poff, ppoff;
     std::vector<InstDev> idev(ctx->inst.size());
     int cut = 512;  // entries per item at most (16 << the current group's lanes_log2)
-    // lanes per item of a group: from the mean (padded) length of its non-empty segments
-    // [s0, s1) of a CSR offset array, so that a sub-warp's item holds about one segment
-    auto lanes_log2 = [](const std::vector<long long> &off, long long s0, long long s1) {
+    // lanes per item of a group: from the mean padded length of its non-empty segments [s0, s1),
+    // counted over every row (also those outside a row slice, so that a sliced context cuts
+    // its items as a full one does), so that a sub-warp's item holds about one segment
+    auto lanes_log2 = [](const std::vector<long long> &plen, long long s0, long long s1) {
         long long tot = 0, n = 0;
         for (long long s = s0; s < s1; ++s)
-            if (off[s + 1] > off[s]) {
-                tot += off[s + 1] - off[s];
+            if (plen[s] > 0) {
+                tot += plen[s];
                 ++n;
             }
         const double mean = n ? (double)tot / (double)n : 0.0;
@@ -735,7 +736,7 @@ int make_plan(rtbte_ctx *ctx) {
             G.stage1_len = q_len;
             G.stage1_src = I.N_off + (long long)nu * I.N_q_pad + q_lo;
             G.stage1_q0 = q_lo;
-            G.lanes_log2 = lanes_log2(I.eph_off, 2LL * blk * I.d.n_c, 2LL * (blk + 1) * I.d.n_c);
+            G.lanes_log2 = lanes_log2(I.eph_plen, 2LL * blk * I.d.n_c, 2LL * (blk + 1) * I.d.n_c);
             cut = 16 << G.lanes_log2;
             G.f_inst = I.f_off;
             G.N_inst = I.N_off;
@@ -769,7 +770,7 @@ int make_plan(rtbte_ctx *ctx) {
         G.n_q_pad = I.N_q_pad;
         G.stage0_len = I.n_c_pad;
         G.stage0_src = I.f_off;
-        G.lanes_log2 = lanes_log2(I.phe_off, 0, I.n_ph);
+        G.lanes_log2 = lanes_log2(I.phe_plen, 0, I.n_ph);
         cut = 16 << G.lanes_log2;
         G.f_inst = I.f_off;
         G.N_inst = I.N_off;
@@ -802,7 +803,7 @@ int make_plan(rtbte_ctx *ctx) {
         G.pp_bits = I.pp_bits;
         G.stage0_len = I.M_pad;
         G.stage0_src = I.P_off;
-        G.lanes_log2 = lanes_log2(I.pp_off, 0, 2 * I.M);
+        G.lanes_log2 = lanes_log2(I.pp_plen, 0, 2 * I.M);
         cut = 16 << G.lanes_log2;
         G.f_inst = I.f_off;
         G.N_inst = I.N_off;
@@ -857,7 +858,7 @@ int make_plan(rtbte_ctx *ctx) {
                                fp64 ? (const void *)rhs_kernel<double, true, false, false, 1>
                                     : (const void *)rhs_kernel<float, true, true, false, 1>};
         for (const void *f : kfns) {
-            RT_CUDA(ctx, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_bytes));
+            RT_CUDA(ctx, allow_max_dynamic_smem(f));
             RT_CUDA(ctx, cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
         }
         const void *kfn = kfns[ctx->wide ? 0 : 1];

@@ -809,12 +809,9 @@ int infer(rtbte_surrogate *s, const double *y, double *dst) {
         return RTBTE_OK;
     }
     if (!s->smem_set) {
-        S_CUDA(s, cudaFuncSetAttribute(infer_conv<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)infer_smem(s->kpad[0], 0)));
-        S_CUDA(s, cudaFuncSetAttribute(infer_conv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)infer_smem(s->kpad[1], 1)));
-        S_CUDA(s, cudaFuncSetAttribute(infer_conv<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)infer_smem(s->kpad[3], 2)));
+        S_CUDA(s, allow_max_dynamic_smem((const void *)infer_conv<0>));
+        S_CUDA(s, allow_max_dynamic_smem((const void *)infer_conv<1>));
+        S_CUDA(s, allow_max_dynamic_smem((const void *)infer_conv<2>));
         s->smem_set = true;
     }
     InferArgs a{};

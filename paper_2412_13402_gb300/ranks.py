@@ -11,9 +11,11 @@ The rt-BTE right-hand side shards two ways:
   slices are all-gathered once per stage; the WRMS error norm is a sum of squares, so one
   scalar all-reduce per attempt gives the global norm.
 
-This module holds the partitioning and reduction arithmetic shared by bench.py and tested on
-CPU ranks (gloo); the GPU runs of this project use one GPU, so only the instance/replica
-form runs on GPUs.
+This module holds the partitioning and reduction arithmetic shared by bench.py and the
+tests.  The row split runs through the library: a rank counts every row's channels
+(Context.upload_channels(count_only=True), Context.row_entries), takes its slice from
+balanced_slices, and creates a Context with row_range=(begin, end), which stores and streams
+only that slice's channels; rtbte_rhs then fills the slice's rows and writes 0 elsewhere.
 """
 from __future__ import annotations
 

@@ -72,6 +72,7 @@ MODELS = {
     "tiny2d_pp2": lambda: ri.tiny((6, 6, 1), pp_stride=2, sigma_pp=0.03),
     "toy2d": lambda: ri.toy2d(),
     "ladder": lambda: ri.ladder(n=6),
+    "ladder3d_fold2": lambda: ri.ladder3d(n=8),
     "graphene36": lambda: ri.graphene_small(36),
     "silicon16": lambda: ri.silicon(16),
 }
@@ -106,18 +107,23 @@ def test_channel_lists_match_oracle(rt, oracle_lib, name, prec):
 
 @pytest.mark.parametrize("parts", [ALL, EPH, PHE, PHPH, FAST])
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp64", 1e-12)])
-@pytest.mark.parametrize("name", ["tiny3d_fold2", "tiny2d_pp2", "toy2d", "graphene36", "silicon16"])
+@pytest.mark.parametrize("name", ["tiny3d_fold2", "tiny2d_pp2", "toy2d", "graphene36", "silicon16", "ladder3d_fold2"])
 def test_rhs_matches_oracle(rt, oracle_lib, name, prec, tol, parts):
     m = MODELS[name]()
     ctx = rt.Context(m, precision=prec)
     ctx.upload_channels()
     o = oracle_lib.Oracle(m)
     o.build_lists()
+    # scale of the rates away from equilibrium: the exact-resonance model's start is an
+    # equilibrium whose oracle RHS is rounding only, so there the error is measured against it
+    scale = np.linalg.norm(o.rhs(np.concatenate(ri.random_populations(m, 9)), parts))
     for y in (m.y0(), sym_state(m, 3), np.concatenate(ri.random_populations(m, 9))):
         ref = o.rhs(y, parts)
         got = ctx.rhs(torch.tensor(y, device="cuda"), parts=parts).cpu().numpy()
         if np.linalg.norm(ref) == 0:
             assert np.abs(got).max() == 0
+        elif np.linalg.norm(ref) < 1e-9 * scale:
+            assert np.linalg.norm(got - ref) <= tol * scale, (name, prec, parts)
         else:
             assert relL2(got, ref) <= tol, (name, prec, parts)
         # rows of parts not requested are exactly zero
@@ -477,3 +483,22 @@ def test_population_range_violations_are_counted(rt):
     assert st["status"] == 0 and st["steps"] == 2
     assert (y[:3] > 1.0).all() and st["range_violations"] == 6
     ctx.close()
+
+
+def test_contexts_of_different_staging_sizes_coexist(rt):
+    """The collision kernel's dynamic shared-memory limit is a property of the kernel function,
+    shared by every context of the process: a context planned later with a smaller staging
+    must not lower it below an earlier context's launches."""
+    big, small = ri.graphene(n=90), ri.graphene_small(24)
+    a = rt.Context(big)
+    a.upload_channels()
+    ya = torch.tensor(big.y0(), device="cuda")
+    ra = a.rhs(ya).cpu().numpy()
+    b = rt.Context(small)
+    b.upload_channels()
+    b.rhs(torch.tensor(small.y0(), device="cuda"))
+    assert np.array_equal(a.rhs(ya).cpu().numpy(), ra)
+    st = a.advance_to(0.01, ya, method="zon43", t0=0.0)
+    assert st["status"] == 0
+    a.close()
+    b.close()

@@ -1,7 +1,8 @@
 """Multi-rank host logic on CPU ranks (gloo, world size 2): whole-job throughput reduction,
-instance sharding, and the row-shard design of one instance's RHS checked with the FP64
-oracle (rows evaluated on separate ranks and all-gathered equal the full RHS; the global
-WRMS norm is one scalar all-reduce)."""
+instance sharding, and the gather / norm arithmetic of the row split of one instance's RHS
+on the FP64 oracle (rows evaluated on separate ranks and all-gathered equal the full RHS;
+the global WRMS norm is one scalar all-reduce).  The same split through librtbte's row-sliced
+contexts is tests/test_gpu_row_shards.py."""
 import os
 import socket
 

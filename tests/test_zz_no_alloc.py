@@ -1,10 +1,12 @@
-"""The allocation-free e-ph entry point (rtbte_eph_rhs_noalloc) agrees with rtbte_rhs.
+"""The allocation-free e-ph entry point (rtbte_eph_rhs_noalloc) agrees with rtbte_rhs and
+with the FP64 oracle.
 
-rtbte_eph_rhs_noalloc is for callers that cannot allocate device memory (code running
-under CUDA graph capture, programs whose device memory belongs to another allocator or a
-pre-reserved arena, latency-critical loops): its working memory is a fixed array in the
-library's device image.  This file is collected last so that a run stopping at its first
-failure has already run every other test; it also passes when run alone.
+rtbte_eph_rhs_noalloc is for callers that cannot allocate device memory (programs whose
+device memory belongs to another allocator or to an arena reserved at start-up,
+latency-critical loops that cannot take an allocation's implicit synchronisation): its
+working memory is a fixed array in the library's device image.  This file is collected last
+so that a run stopping at its first failure has already run every other test; it also passes
+when run alone.
 """
 import ctypes as C
 
@@ -57,6 +59,39 @@ def test_noalloc_eph_matches_rtbte_rhs_twice(rt, mk):
         got = out.cpu().numpy()
         assert relL2(got, ref) <= 1e-5
     ctx.close()
+
+
+def test_noalloc_eph_matches_oracle(rt, oracle_lib):
+    """Two calls in a row against the FP64 oracle's e-ph rows (Eq. e-ph, first integral) on the
+    parity-sized graphene-like model and on the folded 3D exact-resonance model."""
+    lib = rt.load()
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    for m in (ri.graphene_small(36), ri.ladder3d(n=8)):
+        o = oracle_lib.Oracle(m)
+        L = o.build_lists(oracle_lib.EPH)["eph"]
+        # the entry point takes segments (mode, destination, process), sources ascending
+        seg = np.repeat(np.arange(len(L["off"]) - 1), np.diff(L["off"]))
+        key = ((L["ph"] // m.N_q) * m.n_c + seg // 2) * 2 + seg % 2
+        order = np.argsort(key, kind="stable")
+        cnt = np.bincount(key, minlength=2 * m.nmodes * m.n_c)
+        off = np.zeros(cnt.size + 1, np.int64)
+        np.cumsum(cnt, out=off[1:])
+        t_off = torch.tensor(off, device=dev)
+        t_src = torch.tensor(L["src"][order].astype(np.int32), device=dev)
+        t_ph = torch.tensor(L["ph"][order].astype(np.int32), device=dev)
+        t_W = torch.tensor(L["W"][order], dtype=torch.float64, device=dev)
+        out = torch.empty(m.n_c, dtype=torch.float64, device=dev)
+        for seed in (6, 7):
+            y_np = np.concatenate(ri.random_populations(m, seed))
+            y = torch.tensor(y_np, device=dev)
+            rc = lib.rtbte_eph_rhs_noalloc(m.n_c, m.n_ph, m.nmodes, t_off.data_ptr(), t_src.data_ptr(),
+                                           t_ph.data_ptr(), t_W.data_ptr(), y.data_ptr(), out.data_ptr(),
+                                           stream.cuda_stream)
+            assert rc == 0
+            ref = o.rhs(y_np, oracle_lib.EPH)[: m.n_c]
+            assert np.abs(ref).max() > 0
+            assert relL2(out.cpu().numpy(), ref) <= 1e-5
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(rt):

@@ -96,6 +96,8 @@ struct StageArgs {
     unsigned parts;
     int stage;         // -1: populations <- y; 0..S-1: combine stage `stage`
     int respect_done;  // inside an attempt sequence: skip instances whose integration is done
+    const int4 *rblk;  // several instances: row blocks {instance, first row, end row, 0} (else null)
+    int nrblk;
 };
 
 __device__ __forceinline__ double atol_of(const CtlParams &cp, const InstDev &I, long long local) {
@@ -103,50 +105,65 @@ __device__ __forceinline__ double atol_of(const CtlParams &cp, const InstDev &I,
 }
 
 template <class R>
-__global__ void __launch_bounds__(kRedThreads) stage_kernel(RowParams Q, StageArgs a) {
+__device__ __forceinline__ void stage_row(const RowParams &Q, const StageArgs &a, int ii, const InstDev &I, long long c) {
     const int S = a.T.S, i = a.stage;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.n; c += (long long)gridDim.x * blockDim.x) {
-        const int ii = Q.n_inst > 1 ? find_inst(Q, c) : 0;
-        const Ctl *C = a.ctl + ii;
-        if (a.respect_done && C->done) continue;
-        const InstDev I = Q.inst[ii];
-        const long long local = c - I.y_off;
-        const double *y = C->cur ? a.Y1 : a.Y0;
-        if (i < 0) {
-            write_pops<R>(Q, I, local, y[c]);
-            continue;
-        }
-        const double h = C->h_try;
-        double k = row_value<R>(Q, I, local, a.parts);
-        if (a.forcing) k += a.forcing[c];
-        a.K[(long long)i * a.n + c] = k;
-        if (i < S - 1) {
-            double acc = 0.0;
-            for (int j = 0; j <= i; ++j) acc += a.T.A[i + 1][j] * a.K[(long long)j * a.n + c];
-            write_pops<R>(Q, I, local, (R)(y[c] + h * acc));
-        } else {
-            double s1 = 0.0, s2 = 0.0;
-            for (int j = 0; j < S; ++j) {
-                const double kj = a.K[(long long)j * a.n + c];
-                s1 += a.T.b[j] * kj;
-                s2 += (a.T.b[j] - a.T.bt[j]) * kj;
-            }
-            const double ynew = y[c] + h * s1;
-            (C->cur ? a.Y0 : a.Y1)[c] = ynew;
-            // populations outside their physical range (f in [0,1], N >= 0) beyond the absolute
-            // tolerance: counted per attempt, added to the instance's total if it is accepted
-            const bool out = local < I.n_c ? (ynew < -a.cp.atol_c || ynew > 1.0 + a.cp.atol_c) : (ynew < -a.cp.atol_ph);
-            if (out && a.range) atomicAdd(a.range + ii, 1ULL);
-            double x2 = 0.0;
-            if (a.T.has_emb) {  // error weight and weighted error in FP64 (step acceptance reads them)
-                const double w = 1.0 / (a.cp.rtol * fabs(y[c]) + atol_of(a.cp, I, local));
-                const double x = h * s2 * w;
-                x2 = x * x;
-            }
-            if (!isfinite(ynew)) x2 = __longlong_as_double(0x7ff8000000000000LL);
-            a.wsq[c] = x2;
-        }
+    const Ctl *C = a.ctl + ii;
+    const long long local = c - I.y_off;
+    const double *y = C->cur ? a.Y1 : a.Y0;
+    if (i < 0) {
+        write_pops<R>(Q, I, local, y[c]);
+        return;
     }
+    const double h = C->h_try;
+    double k = row_value<R>(Q, I, local, a.parts);
+    if (a.forcing) k += a.forcing[c];
+    a.K[(long long)i * a.n + c] = k;
+    if (i < S - 1) {
+        double acc = 0.0;
+        for (int j = 0; j <= i; ++j) acc += a.T.A[i + 1][j] * a.K[(long long)j * a.n + c];
+        write_pops<R>(Q, I, local, (R)(y[c] + h * acc));
+    } else {
+        double s1 = 0.0, s2 = 0.0;
+        for (int j = 0; j < S; ++j) {
+            const double kj = a.K[(long long)j * a.n + c];
+            s1 += a.T.b[j] * kj;
+            s2 += (a.T.b[j] - a.T.bt[j]) * kj;
+        }
+        const double ynew = y[c] + h * s1;
+        (C->cur ? a.Y0 : a.Y1)[c] = ynew;
+        // populations outside their physical range (f in [0,1], N >= 0) beyond the absolute
+        // tolerance: counted per attempt, added to the instance's total if it is accepted
+        const bool out = local < I.n_c ? (ynew < -a.cp.atol_c || ynew > 1.0 + a.cp.atol_c) : (ynew < -a.cp.atol_ph);
+        if (out && a.range) atomicAdd(a.range + ii, 1ULL);
+        double x2 = 0.0;
+        if (a.T.has_emb) {  // error weight and weighted error in FP64 (step acceptance reads them)
+            const double w = 1.0 / (a.cp.rtol * fabs(y[c]) + atol_of(a.cp, I, local));
+            const double x = h * s2 * w;
+            x2 = x * x;
+        }
+        if (!isfinite(ynew)) x2 = __longlong_as_double(0x7ff8000000000000LL);
+        a.wsq[c] = x2;
+    }
+}
+
+// Stage combination over the rows.  Several instances: the grid walks a table of row blocks of
+// one instance each, so a finished instance's blocks are skipped whole and no row looks up its
+// instance; one instance: a grid-stride loop over its rows.
+template <class R>
+__global__ void __launch_bounds__(kRedThreads) stage_kernel(RowParams Q, StageArgs a) {
+    if (a.rblk) {
+        for (int b = blockIdx.x; b < a.nrblk; b += gridDim.x) {
+            const int4 t = a.rblk[b];
+            if (a.respect_done && a.ctl[t.x].done) continue;
+            const InstDev I = Q.inst[t.x];
+            for (long long c = t.y + threadIdx.x; c < t.z; c += blockDim.x) stage_row<R>(Q, a, t.x, I, c);
+        }
+        return;
+    }
+    const InstDev I = Q.inst[0];
+    if (a.respect_done && a.ctl[0].done) return;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.n; c += (long long)gridDim.x * blockDim.x)
+        stage_row<R>(Q, a, 0, I, c);
 }
 
 // Fixed-order sum of v[b .. b+n) by one block.
@@ -420,7 +437,8 @@ int n_inst(rtbte_ctx *ctx) { return (int)ctx->inst.size(); }
 
 template <class R>
 int launch_stage(rtbte_ctx *ctx, const StageArgs &a, cudaStream_t s) {
-    stage_kernel<R><<<row_grid(ctx), kRedThreads, 0, s>>>(row_params(ctx), a);
+    const int grid = a.rblk ? std::min(a.nrblk, 8 * ctx->num_sms) : row_grid(ctx);
+    stage_kernel<R><<<grid, kRedThreads, 0, s>>>(row_params(ctx), a);
     RT_CUDA(ctx, cudaGetLastError());
     ctx->launches++;
     return RTBTE_OK;
@@ -444,6 +462,10 @@ StageArgs stage_args(rtbte_ctx *ctx, const Tableau &T, const CtlParams &cp, unsi
     a.wsq = ctx->wrms_part.as<double>();
     a.n = ctx->n_y;
     a.parts = parts;
+    if (n_inst(ctx) > 1) {
+        a.rblk = ctx->rblk.as<int4>();
+        a.nrblk = ctx->n_rblk;
+    }
     return a;
 }
 

@@ -213,7 +213,9 @@ struct rtbte_ctx {
     rtbte::DevBuf popf, popN, popP, instdev, compact;
     // execution plan of the RHS
     bool plan_valid = false;
-    rtbte::DevBuf items, groups, partials, eoff, poff, ppoff, cta_tab, wpre, dyn_tab;
+    rtbte::DevBuf items, groups, partials, eoff, poff, ppoff, cta_tab, gwt, dyn_tab;
+    rtbte::DevBuf rblk;  // several instances: row blocks {instance, first row, end row, 0} of the stage kernels
+    int n_rblk = 0;
     int n_items = 0, n_groups = 0;
     int part_items[3] = {0, 0, 0};
     int part_first[3] = {0, 0, 0};

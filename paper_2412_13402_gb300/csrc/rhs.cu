@@ -54,6 +54,8 @@ struct KParams {
     void *partials;
     const void *popf, *popN, *popP;
     const Ctl *ctl;  // per-instance controllers: launches inside an integrator skip finished instances
+    const int *act;      // batched integration: active groups in order (-1 ends), else null
+    const int *cta_act;  // batched integration: index in act[] of each CTA's first group
     const int4 *tail;  // dynamic chunks {first item, end item, group, 0} after the static ranges
     int n_tail;
     int *tail_ctr;     // [0] next chunk to take, [1] CTAs finished (reset by the last one)
@@ -439,25 +441,31 @@ __global__ void __launch_bounds__(kRhsThreads, MINB) rhs_kernel(KParams P) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     int staged = -1;
     const int ra = P.cta_items[blockIdx.x], rb = P.cta_items[blockIdx.x + 1];
-    int g = P.n_groups;  // next group of the static range
+    int g = P.n_groups;  // next group of the static range (with P.act: next index into act[])
     if (ra < rb) {
-        int lo = 0, hi = P.n_groups - 1;  // last group with item_begin <= ra
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (P.groups[mid].item_begin <= ra) lo = mid; else hi = mid - 1;
+        if (P.act) {
+            g = P.cta_act[blockIdx.x];
+        } else {
+            int lo = 0, hi = P.n_groups - 1;  // last group with item_begin <= ra
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (P.groups[mid].item_begin <= ra) lo = mid; else hi = mid - 1;
+            }
+            g = lo;
         }
-        g = lo;
     }
     bool dynamic = false;
     for (;;) {
         int ug, ua, ub;  // next unit of work: items [ua, ub) of group ug
         if (!dynamic) {
-            if (g >= P.n_groups || P.groups[g].item_begin >= rb) {
+            const int gg = !P.act ? g : (g < P.n_groups ? P.act[g] : -1);
+            if (gg < 0 || gg >= P.n_groups || P.groups[gg].item_begin >= rb) {
                 dynamic = true;
                 if (P.n_tail == 0) break;
                 continue;
             }
-            ug = g++;
+            ug = gg;
+            ++g;
             ua = max(ra, P.groups[ug].item_begin);
             ub = min(rb, P.groups[ug].item_end);
             if (ua >= ub) continue;
@@ -490,54 +498,93 @@ __global__ void __launch_bounds__(kRhsThreads, MINB) rhs_kernel(KParams P) {
 }
 
 // Work split over the groups still active (instance not done, part in the mask), recomputed
-// on the device before a collision launch inside a batched integration: CTA c gets the items
-// whose cumulative active weight falls in [c, c+1) * total / grid.  One block.
-__global__ void split_kernel(const Group *groups, int n_groups, const long long *wpre, const Ctl *ctl, unsigned mask,
-                             int grid, int n_items, int *out) {
-    __shared__ long long A[1025];
+// on the device before a collision launch inside a batched integration.  One block:
+//   - the active groups are listed in order in act[] (terminated by -1);
+//   - CTA c gets the active weight [c, c+1) * total / grid: out[c] is its first item, found by
+//     interpolating linearly within the active group holding that weight (items of one group
+//     carry similar weights; the split affects balance only, never results), and out_act[c]
+//     the index in act[] of that group;
+//   - out[grid] is the end of the last active group's items.
+// A CTA then visits only the active groups act[out_act[c]], ... overlapping its item range,
+// so finished instances cost it nothing.
+__global__ void split_kernel(const Group *groups, int n_groups, const long long *gw, const Ctl *ctl, unsigned mask,
+                             int grid, int *out, int *out_act, int *act) {
+    __shared__ long long A[1025];   // inclusive prefix of active weight over groups (A[0] = 0)
+    __shared__ int Cn[1025];        // active groups before group g
     __shared__ long long wsum[32];
+    __shared__ int csum[32];
     const int T = blockDim.x;  // 256 threads, n_groups <= 1024 (checked on the host)
-    // active weight of each group, then an inclusive prefix over the groups: each thread scans
-    // a run of C consecutive groups, the run totals are scanned across the block (warp
-    // shuffles, then the warp totals), and each run adds the total before it
     const int C = (n_groups + T - 1) / T;
     const int g0 = threadIdx.x * C;
     long long run = 0;
+    int nrun = 0;
     for (int g = g0; g < g0 + C && g < n_groups; ++g) {
         const Group &G = groups[g];
-        const bool on = (mask & (1u << G.part)) && !ctl[G.inst].done;
-        run += on ? wpre[G.item_end] - wpre[G.item_begin] : 0;
+        const bool on = (mask & (1u << G.part)) && !ctl[G.inst].done && G.item_end > G.item_begin;
+        run += on ? gw[g] : 0;
+        nrun += on ? 1 : 0;
         A[g + 1] = run;
+        Cn[g + 1] = nrun;
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     long long incl = run;
+    int nincl = nrun;
     for (int o = 1; o < 32; o <<= 1) {
         const long long v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
+        const int nv = __shfl_up_sync(0xffffffffu, nincl, o);
+        if (lane >= o) {
+            incl += v;
+            nincl += nv;
+        }
     }
-    if (lane == 31) wsum[wid] = incl;
-    if (threadIdx.x == 0) A[0] = 0;
+    if (lane == 31) {
+        wsum[wid] = incl;
+        csum[wid] = nincl;
+    }
+    if (threadIdx.x == 0) {
+        A[0] = 0;
+        Cn[0] = 0;
+    }
     __syncthreads();
     if (wid == 0) {
         long long w = lane < (T >> 5) ? wsum[lane] : 0;
+        int nw = lane < (T >> 5) ? csum[lane] : 0;
         for (int o = 1; o < 32; o <<= 1) {
             const long long v = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += v;
+            const int nv = __shfl_up_sync(0xffffffffu, nw, o);
+            if (lane >= o) {
+                w += v;
+                nw += nv;
+            }
         }
-        if (lane < (T >> 5)) wsum[lane] = w;
+        if (lane < (T >> 5)) {
+            wsum[lane] = w;
+            csum[lane] = nw;
+        }
     }
     __syncthreads();
     const long long before = incl - run + (wid > 0 ? wsum[wid - 1] : 0);
-    for (int g = g0; g < g0 + C && g < n_groups; ++g) A[g + 1] += before;
+    const int nbefore = nincl - nrun + (wid > 0 ? csum[wid - 1] : 0);
+    for (int g = g0; g < g0 + C && g < n_groups; ++g) {
+        A[g + 1] += before;
+        Cn[g + 1] += nbefore;
+    }
     __syncthreads();
     const long long total = A[n_groups];
+    const int n_act = Cn[n_groups];
+    for (int g = threadIdx.x; g < n_groups; g += T)  // compact list of the active groups
+        if (Cn[g + 1] > Cn[g]) act[Cn[g]] = g;
+    if (threadIdx.x == 0) act[n_act] = -1;
     for (int c = threadIdx.x; c <= grid; c += T) {
         if (total == 0) {
             out[c] = 0;
+            if (c < grid) out_act[c] = 0;
             continue;
         }
-        if (c == grid) {
-            out[c] = n_items;
+        if (c == grid) {  // end of the last active group's items
+            int last = n_groups - 1;
+            while (last > 0 && Cn[last + 1] == Cn[last]) --last;
+            out[c] = groups[last].item_end;
             continue;
         }
         const long long t = total * c / grid;
@@ -548,13 +595,10 @@ __global__ void split_kernel(const Group *groups, int n_groups, const long long 
         }
         while (lo < n_groups - 1 && A[lo + 1] == A[lo]) ++lo;  // skip inactive groups
         const Group &G = groups[lo];
-        const long long w = wpre[G.item_begin] + (t - A[lo]);
-        int a = G.item_begin, b = G.item_end;  // first item with wpre >= w
-        while (a < b) {
-            int mid = (a + b) >> 1;
-            if (wpre[mid] < w) a = mid + 1; else b = mid;
-        }
-        out[c] = c == 0 ? 0 : a;
+        const long long wg = A[lo + 1] - A[lo];
+        const long long ni = G.item_end - G.item_begin;
+        out[c] = G.item_begin + (int)((t - A[lo]) * ni / (wg > 0 ? wg : 1));
+        out_act[c] = Cn[lo];
     }
 }
 
@@ -673,8 +717,13 @@ int split_tables(rtbte_ctx *ctx, int overhead) {
         ctx->tail_off[mask] = (int)tail.size();
     }
     ctx->item_overhead = overhead;
+    std::vector<long long> gwt(ctx->group_begin_h.size());  // weight of each group's items
+    for (size_t g = 0; g < gwt.size(); ++g) {
+        const int e = g + 1 < ctx->group_begin_h.size() ? ctx->group_begin_h[g + 1] : n;
+        gwt[g] = wpre[e] - wpre[ctx->group_begin_h[g]];
+    }
     int rc;
-    if ((rc = upload_vec(ctx, ctx->wpre, wpre))) return rc;
+    if ((rc = upload_vec(ctx, ctx->gwt, gwt))) return rc;
     if (tail.empty()) tail.push_back(make_int4(0, 0, 0, 0));
     if ((rc = upload_vec(ctx, ctx->tail_tab, tail))) return rc;
     return upload_vec(ctx, ctx->cta_tab, tab);
@@ -890,11 +939,22 @@ int make_plan(rtbte_ctx *ctx) {
     if ((rc = upload_vec(ctx, ctx->ppoff, ppoff))) return rc;
     if ((rc = upload_vec(ctx, ctx->instdev, idev))) return rc;
     if ((rc = upload_vec(ctx, ctx->compact, compact))) return rc;
+    std::vector<int4> rblk;  // row blocks of 1024 rows within one instance (batched stage kernels)
+    if (ctx->inst.size() > 1)
+        for (size_t i = 0; i < ctx->inst.size(); ++i) {
+            const InstHost &I = ctx->inst[i];
+            const long long e = I.y_off + I.d.n_c + I.n_ph;
+            for (long long r = I.y_off; r < e; r += 1024)
+                rblk.push_back(make_int4((int)i, (int)r, (int)std::min(e, r + 1024), 0));
+        }
+    if (ctx->n_y >= (long long)INT32_MAX) return fail(ctx, RTBTE_E_UNSUPPORTED, "state vector too long");
+    ctx->n_rblk = (int)rblk.size();
+    if ((rc = upload_vec(ctx, ctx->rblk, rblk))) return rc;
     if ((rc = split_tables(ctx, ctx->item_overhead))) return rc;
     if (ctx->n_groups > 1024) return fail(ctx, RTBTE_E_UNSUPPORTED, "more than 1024 staging groups");
     ctx->dyn_tab.release();
-    RT_CUDA(ctx, cudaMalloc(&ctx->dyn_tab.p, sizeof(int) * (ctx->grid + 1)));
-    ctx->dyn_tab.bytes = sizeof(int) * (ctx->grid + 1);
+    ctx->dyn_tab.bytes = sizeof(int) * (2 * ctx->grid + 1 + ctx->n_groups + 1);
+    RT_CUDA(ctx, cudaMalloc(&ctx->dyn_tab.p, ctx->dyn_tab.bytes));
     ctx->partials.release();
     size_t pb = std::max<size_t>(2 * R * (size_t)std::max(ctx->n_items, 1), 16);
     RT_CUDA(ctx, cudaMalloc(&ctx->partials.p, pb));
@@ -928,11 +988,14 @@ static int launch_core_t(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStr
     P.mask = parts;
     P.pf_dist = ctx->pf_dist;
     if (ctl && ctx->inst.size() > 1) {  // batched integration: balance over the active instances
-        split_kernel<<<1, 256, 0, s>>>(ctx->groups.as<Group>(), ctx->n_groups, ctx->wpre.as<long long>(), ctl, parts,
-                                       ctx->grid, ctx->n_items, ctx->dyn_tab.as<int>());
+        int *dt = ctx->dyn_tab.as<int>();  // [grid+1] item bounds, [grid] act indices, [n_groups+1] act
+        split_kernel<<<1, 256, 0, s>>>(ctx->groups.as<Group>(), ctx->n_groups, ctx->gwt.as<long long>(), ctl, parts,
+                                       ctx->grid, dt, dt + ctx->grid + 1, dt + 2 * ctx->grid + 1);
         RT_CUDA(ctx, cudaGetLastError());
         ctx->launches++;
-        P.cta_items = ctx->dyn_tab.as<int>();
+        P.cta_items = dt;
+        P.cta_act = dt + ctx->grid + 1;
+        P.act = dt + 2 * ctx->grid + 1;
     } else {
         P.cta_items = ctx->cta_tab.as<int>() + (long long)(parts - 1) * (ctx->grid + 1);
         P.tail = ctx->tail_tab.as<int4>() + ctx->tail_off[parts - 1];

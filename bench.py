@@ -72,9 +72,11 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: only standalone full-RHS evaluations (warm-up + steps), no JSON line")
     ap.add_argument("--grid", type=int, default=180, help="k/q grid side of the graphene-like workload (profiling)")
-    ap.add_argument("--workload", default="graphene", choices=["graphene", "silicon_printed", "ensemble16", "ensemble"],
+    ap.add_argument("--workload", default="graphene",
+                    choices=["graphene", "silicon_printed", "ensemble16", "ensemble", "surrogate"],
                     help="workload of --profile: the graphene-like one at --grid, config 3 at the printed grids, "
-                         "the first 16 ensemble instances, or all 64")
+                         "the first 16 ensemble instances, all 64, or the learned slow stage of the graphene-like "
+                         "workload (training steps of batch 8, then inferences)")
     ap.add_argument("--parts", type=int, default=7, help="RHS parts of --profile launches (1 e-ph, 2 ph-e, 4 ph-ph)")
     return ap.parse_args()
 
@@ -92,6 +94,8 @@ def run_profile(args):
 
     import numpy as np
 
+    if args.workload == "surrogate":
+        return run_profile_surrogate(args)
     if args.workload.startswith("ensemble"):
         ms = ri.ensemble()[:16] if args.workload == "ensemble16" else ri.ensemble()
         ctx = rt.Context(ms, precision="fp32")
@@ -121,6 +125,47 @@ def run_profile(args):
     t = ms_ / max(n, 1)
     print(f"profile workload={name} parts={parts} entries={ent} tuning={ctx.tuning()} rhs_kernel_avg_ms={t:.4f} "
           f"alg_GBps={8.0 * ent / t / 1e6:.1f}", flush=True)
+    ctx.close()
+    return 0
+
+
+def run_profile_surrogate(args):
+    """The learned slow stage's kernels for ncu captures: 32 (N, exact I^{ph-ph}) pairs along
+    the graphene-like workload's trajectory, `--warmup` then `--steps` training steps of batch 8
+    (forward layers and input gradients on the tensor-core GEMM engine, where the device has it),
+    then `--steps` inferences; prints training steps per second for both GEMM engines."""
+    import torch
+
+    import paper_2412_13402_gb300 as rt
+    import rtbte_inputs as ri
+
+    m = ri.graphene()
+    ctx = rt.Context(m, precision="fp32")
+    ctx.upload_channels()
+    y = torch.tensor(m.y0(), device="cuda")
+    sur = rt.Surrogate(ctx, width=64, capacity=32, seed=1)
+    t = 0.0
+    for i in range(32):
+        sur.collect(y, 0)
+        ctx.advance_to(t + 0.002, y, method="zon43", t0=t, resume=1 if i else 0, **TOL)
+        t += 0.002
+    rates = {}
+    for engine in (1, 0):
+        try:
+            sur.set_gemm(engine)
+        except rt.RtbteError:
+            continue
+        sur.train(max(args.warmup, 1), 8, 1e-4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sur.train(max(args.steps, 1), 8, 1e-4)
+        torch.cuda.synchronize()
+        rates["tcgen05" if engine == 0 else "mma.sync"] = max(args.steps, 1) / (time.perf_counter() - t0)
+    for _ in range(max(args.steps, 1)):
+        sur.predict(y)
+    torch.cuda.synchronize()
+    print(f"profile workload=surrogate train_steps_per_s_batch8={rates}", flush=True)
+    sur.close()
     ctx.close()
     return 0
 
@@ -865,20 +910,29 @@ def silicon_long_study(rt, ri, dev, t_end=20.0, window=1.0):
     return out
 
 
-def surrogate_study(rt, ri, dev, t_end=0.5, h_s=0.020, period=10):
-    """The learned slow stage on the same workload and error protocol.  Pairs (N, exact
-    I^{ph-ph}) come from the method's own trajectories (6 initial conditions, 21 states
-    each, 10 fs apart); the network (4 periodic 3x3 conv layers of width 64, pointwise MLP)
-    is trained by librtbte's BF16 tensor-core kernels, first on single pairs, then on
-    differences along a trajectory.  A/B over t_end: plain MRI (exact slow part at every
-    stage), MRI with the surrogate's control variate (exact judge every `period` slow steps),
-    and the same schedule with the network's output zeroed (the exact value held between
-    judges), errors against the FP64 reference."""
+def surrogate_study(rt, ri, dev, t_end=0.5, n_traj=40, states_per=500, dt_collect=0.004):
+    """Config 5, the learned slow stage, at the accuracy the target asks for (population error
+    <= 1e-6 over 0.5 ps against the FP64 reference of the error protocol).
+    1. Pairs (N, exact I^{ph-ph}) from the method's own trajectories: n_traj initial conditions of
+       the graphene-like workload (E_x 0.3-1.0 eV, amplitude 0.1-0.4, T 200-400 K, drawn from
+       the seed), states every dt_collect along adaptive Zonneveld: n_traj * states_per pairs.
+    2. Training by librtbte's BF16 tensor-core kernels: single pairs, then differences of pairs of
+       one trajectory (the quantity the control variate uses).
+    3. The error of the slow value along a trajectory: the exact value held from a reference
+       state, and the control variate I(Y_ref) + S(Y) - S(Y_ref), 10-200 fs after the reference.
+    4. The judge tolerance tied to the target: a relative error eps of the slow value over a
+       judge period T moves the phonon populations by about eps * T * |I^{ph-ph}| / |N|
+       (relative), so eps <= 1e-6 / (T |I^{ph-ph}|/|N|).
+    5. A/B over t_end at the MRI settings of the error protocol (h_s 20 fs and 100 fs, fast rtol
+       1e-4): plain MRI against surrogate MRI with the exact judge every 10 or every slow step at
+       that tolerance (fallbacks counted), and with the tolerance unbounded (never detached);
+       plus the slow part's share of plain MRI's kernel time, the most any surrogate can save."""
     import numpy as np
     import torch
 
     m = ri.graphene()
     nc = m.n_c
+    full = m.pp_full_index() + nc
     ctx = rt.Context(m, precision="fp32", device=dev.index or 0)
     ctx.upload_channels()
     ctx.autotune(rt.RTBTE_ALL)
@@ -892,6 +946,27 @@ def surrogate_study(rt, ri, dev, t_end=0.5, h_s=0.020, period=10):
         ref_ctx.close()
         _REFERENCE[t_end] = yr.cpu().numpy()
     ref = _REFERENCE[t_end]
+    rng = np.random.default_rng(13402 * 10 + 5)
+    sur = rt.Surrogate(ctx, width=64, capacity=n_traj * states_per, seed=3)
+    t0 = time.time()
+    for j in range(n_traj):
+        mj = ri.graphene(E_x=float(rng.uniform(0.3, 1.0)), amp=float(rng.uniform(0.1, 0.4)),
+                         T=float(rng.uniform(200.0, 400.0)))
+        yj = torch.tensor(mj.y0(), device=dev)
+        sur.collect(yj, j)
+        t = 0.0
+        for i in range(1, states_per):
+            st = ctx.advance_to(t + dt_collect, yj, t0=t, method="zon43", resume=1 if i > 1 else 0, **TOL)
+            assert st["status"] == 0
+            t += dt_collect
+            sur.collect(yj, j)
+    torch.cuda.synchronize()
+    collect_s = time.time() - t0
+    t0 = time.time()
+    l_abs = sur.train(4000, 8, 1e-3)
+    l_diff = sur.train(4000, 8, 5e-4, horizon=4)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
 
     def timed(fn, n):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -905,59 +980,72 @@ def surrogate_study(rt, ri, dev, t_end=0.5, h_s=0.020, period=10):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / n
 
-    t0 = time.time()
-    states = []
-    for j in range(6):
-        mj = ri.graphene(E_x=0.5 + 0.1 * j, amp=0.15 + 0.05 * j, T=220.0 + 30 * j)
-        yj = torch.tensor(mj.y0(), device=dev)
-        states.append((yj.clone(), j))
-        for i in range(1, 21):
-            assert ctx.advance_to(0.01 * i, yj, t0=0.01 * (i - 1), method="zon43", **TOL)["status"] == 0
-            states.append((yj.clone(), j))
-    sur = rt.Surrogate(ctx, width=64, capacity=len(states), seed=3)
-    for yy, j in states:
-        sur.collect(yy, j)
-    torch.cuda.synchronize()
-    collect_s = time.time() - t0
-    t0 = time.time()
-    l_abs = sur.train(2000, 4, 1e-3)
-    l_diff = sur.train(2000, 4, 5e-4, horizon=4)
-    train_s = time.time() - t0
     yd = torch.empty_like(y0)
     exact_ms = timed(lambda: ctx.rhs(y0, yd, parts=rt.RTBTE_SLOW), 50)
+    fast_ms = timed(lambda: ctx.rhs(y0, yd, parts=rt.RTBTE_FAST), 50)
     infer_ms = timed(lambda: sur.predict(y0), 50)
+    # slow value along a test trajectory (not collected): held exact value and control variate
+    mt = ri.graphene(E_x=0.75, amp=0.25, T=300.0)
+    yt = torch.tensor(mt.y0(), device=dev)
+    traj = [yt.clone()]
+    t = 0.0
+    for i in range(40):
+        ctx.advance_to(t + 0.01, yt, t0=t, method="zon43", resume=1 if i else 0, **TOL)
+        t += 0.01
+        traj.append(yt.clone())
+    slow_err = []
+    for r in (0, 20):
+        Ir = ctx.rhs(traj[r], parts=rt.RTBTE_SLOW)[full].cpu().numpy()
+        Sr = sur.predict(traj[r])[full].cpu().numpy()
+        for d in (1, 2, 5, 10, 20):
+            It = ctx.rhs(traj[r + d], parts=rt.RTBTE_SLOW)[full].cpu().numpy()
+            St = sur.predict(traj[r + d])[full].cpu().numpy()
+            slow_err.append({"ref_fs": 10 * r, "dt_fs": 10 * d,
+                             "held": float(np.linalg.norm(It - Ir) / np.linalg.norm(It)),
+                             "control_variate": float(np.linalg.norm(It - (Ir + St - Sr)) / np.linalg.norm(It))})
+    ratio = float(np.linalg.norm(ctx.rhs(y0, parts=rt.RTBTE_SLOW).cpu().numpy()[nc:]) / np.linalg.norm(m.N0))
 
-    def run(tag, attach):
-        if attach:
-            sur.attach(judge_period=period, judge_tol=10.0)
+    def run(tag, h_s, period=None, tol=None):
+        if period is not None:
+            sur.attach(judge_period=period, judge_tol=tol)
+        kw = dict(t0=0.0, method="mri", h_s=h_s, rtol=1e-4, atol_c=1e-9, atol_ph=1e-12)
+        ctx.advance_to(t_end, y0.clone(), **kw)  # untimed: graph capture
         y = y0.clone()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(ctx.stream)
-        st = ctx.advance_to(t_end, y, t0=0.0, method="mri", h_s=h_s, **TOL)
+        st = ctx.advance_to(t_end, y, **kw)
         e1.record(ctx.stream)
         torch.cuda.synchronize()
-        sur.detach()
+        if period is not None:
+            sur.detach()
         sec = e0.elapsed_time(e1) / 1000.0
         yy = y.cpu().numpy()
-        return {"variant": tag, "status": st["status"], "seconds": sec, "sim_ps_per_s": t_end / sec,
+        return {"variant": tag, "h_s_fs": 1000 * h_s, "judge_period": period, "judge_tol": tol, "status": st["status"],
+                "seconds": sec, "sim_ps_per_s": t_end / sec,
                 "err_carriers": float(np.linalg.norm(yy[:nc] - ref[:nc]) / np.linalg.norm(ref[:nc])),
                 "err_phonons": float(np.linalg.norm(yy[nc:] - ref[nc:]) / np.linalg.norm(ref[nc:])),
                 "slow_exact": st["slow_exact"], "slow_surrogate": st["slow_surrogate"],
-                "judge_err_max": st["judge_err_max"], "rhs_fast": st["rhs_fast"]}
+                "fallbacks": st["surrogate_fallbacks"], "judge_err_max": st["judge_err_max"],
+                "rhs_fast": st["rhs_fast"]}
 
-    ab = [run("plain MRI", False), run("surrogate MRI", True)]
-    p = sur.get_params()
-    held = p.copy()
-    held[-(64 * m.nmodes + m.nmodes):] = 0.0
-    sur.set_params(held)
-    ab.append(run("held exact value (network output zeroed)", True))
-    sur.set_params(p)
+    ab = []
+    for h_s in (0.020, 0.100):
+        ab.append(run("plain MRI", h_s))
+        for period in (10, 1):
+            tol = 1e-6 / (period * h_s * ratio)
+            ab.append(run("surrogate MRI, judge tolerance from the 1e-6 target", h_s, period, tol))
+        ab.append(run("surrogate MRI, never detached", h_s, 10, 1e30))
+    plain = {r["h_s_fs"]: r for r in ab if r["variant"] == "plain MRI"}
+    slow_share = {f"h_s_{int(k)}fs": (v["slow_exact"] * exact_ms) / (v["slow_exact"] * exact_ms + v["rhs_fast"] * fast_ms)
+                  for k, v in plain.items()}
     sur.close()
     ctx.close()
-    return {"pairs": len(states), "collect_s": collect_s, "train_steps": [2000, 2000], "batch": 4, "train_s": train_s,
-            "loss_abs": l_abs, "loss_diff": l_diff, "exact_slow_ms": exact_ms, "inference_ms": infer_ms,
-            "t_end_ps": t_end, "h_s_fs": h_s * 1000, "judge_period": period, "ab": ab}
+    return {"pairs": n_traj * states_per, "trajectories": n_traj, "collect_s": collect_s, "train_steps": [4000, 4000],
+            "batch": 8, "train_s": train_s, "loss_abs": l_abs, "loss_diff": l_diff, "exact_slow_ms": exact_ms,
+            "fast_rhs_ms": fast_ms, "inference_ms": infer_ms, "slow_value_error": slow_err,
+            "I_pp_over_N_per_ps": ratio, "slow_share_of_plain_mri_kernel_time": slow_share, "t_end_ps": t_end,
+            "ab": ab}
 
 
 def headline(*, value, n_gpus, steps, warmup, ms_per_step, config, sim_ps_per_s, sim_ps_at_1e6, roofline, e2e,

@@ -447,6 +447,14 @@ void rtbte_surrogate_stats(const rtbte_surrogate *s, float *mu, float *sd, float
  * Errors: INVALID_ARG, STATE (untrained), UNSUPPORTED. */
 int rtbte_set_surrogate(rtbte_ctx *ctx, rtbte_surrogate *s, int judge_period, double judge_tol);
 
+/* GEMM engine of the surrogate's training and batched forward passes: 0 (the default where the
+ * device has them) = fifth-generation tensor cores (tcgen05.mma, accumulator in tensor memory,
+ * operand tiles by TMA with 128-byte swizzle) for the forward layers, the input gradients and
+ * (widths that are multiples of 64) the weight gradients; mma.sync for the rest; 1 = mma.sync for
+ * every product.  Both use BF16 operands and FP32 accumulation.  Errors: INVALID_ARG,
+ * UNSUPPORTED (engine 0 on a device without tcgen05), STATE. */
+int rtbte_surrogate_set_gemm(rtbte_surrogate *s, int engine);
+
 /* Release the surrogate's device memory (NULL is ignored). */
 void rtbte_surrogate_destroy(rtbte_surrogate *s);
 

@@ -38,7 +38,8 @@ EXPORTS = ["rtbte_desc_defaults", "rtbte_integ_defaults", "rtbte_create", "rtbte
            "rtbte_status_string", "rtbte_eph_rhs_noalloc", "rtbte_surrogate_create", "rtbte_surrogate_collect",
            "rtbte_surrogate_train", "rtbte_surrogate_predict", "rtbte_surrogate_loss_grad",
            "rtbte_surrogate_num_params", "rtbte_surrogate_get_params", "rtbte_surrogate_set_params",
-           "rtbte_surrogate_stats", "rtbte_set_surrogate", "rtbte_surrogate_destroy", "rtbte_destroy"]
+           "rtbte_surrogate_stats", "rtbte_set_surrogate", "rtbte_surrogate_set_gemm", "rtbte_surrogate_destroy",
+           "rtbte_destroy"]
 
 
 class InstanceDesc(C.Structure):
@@ -160,6 +161,7 @@ def load():
         L.rtbte_surrogate_stats.argtypes = [vp, vp, vp, vp, vp]
         L.rtbte_surrogate_stats.restype = None
         L.rtbte_set_surrogate.argtypes = [vp, vp, i32, dbl]
+        L.rtbte_surrogate_set_gemm.argtypes = [vp, i32]
         L.rtbte_surrogate_destroy.argtypes = [vp]
         L.rtbte_surrogate_destroy.restype = None
         L.rtbte_destroy.argtypes = [vp]
@@ -522,6 +524,10 @@ class Surrogate:
         n = C.c_int()
         load().rtbte_surrogate_stats(self.h, mu.ctypes.data, sd.ctypes.data, so.ctypes.data, C.byref(n))
         return mu, sd, so, n.value
+
+    def set_gemm(self, engine: int):
+        """0: tcgen05 tensor cores where both operands are K-major (default); 1: mma.sync for all."""
+        self._chk(load().rtbte_surrogate_set_gemm(self.h, engine))
 
     def attach(self, judge_period: int = 10, judge_tol: float = 1e-2):
         """Use this surrogate for the slow part of the context's MRI integrations."""

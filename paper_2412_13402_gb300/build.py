@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librtbte.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "builder.cu", "rhs.cu", "integrate.cu", "noalloc.cu", "surrogate.cu"]
-HEADERS = ["internal.cuh", "rows.cuh"]
+HEADERS = ["internal.cuh", "rows.cuh", "umma.cuh"]
 
 
 def nvcc() -> str:

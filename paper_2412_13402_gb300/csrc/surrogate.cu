@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "umma.cuh"
 
 using namespace rtbte;
 
@@ -551,6 +552,9 @@ struct rtbte_surrogate {
         lossp, ydot;
     DevBuf Eref, out_ref, normp;  // control-variate reference [Pq][C]: exact value, network output
     DevBuf wbt, a0, a1;           // transposed BF16 weights and activations of the fused inference path
+    DevBuf wtt, tcerr;            // K-major BF16 weights of the tensor-core GEMMs (W_l^T, M1^T, M2^T); error word
+    long long off_tt[kLayers + 2] = {0, 0, 0, 0, 0, 0};
+    int engine = 0;               // 0: tcgen05 GEMMs where both operands are K-major; 1: mma.sync everywhere
     long long off_t[kLayers + 1] = {0, 0, 0, 0, 0};
     bool has_ref = false, fused = false, smem_set = false;
     std::vector<int> traj;        // trajectory id of each collected pair
@@ -606,6 +610,157 @@ int gemm(rtbte_surrogate *s, const bf16 *A, int lda, const bf16 *B, int ldb, flo
     return RTBTE_OK;
 }
 
+// ---- tcgen05 GEMMs ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// TMA map of a K-major BF16 matrix [rows x cols] (row stride ld elements), boxes of 64 columns x
+// box_rows rows, 128-byte swizzle, zero fill outside
+bool kmajor_map(CUtensorMap *m, const bf16 *ptr, long long rows, long long cols, long long ld, int box_rows) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(bf16)};
+    const cuuint32_t box[2] = {(cuuint32_t)umma::kTK, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(ptr), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// C[M x N] = A[M x K] B[N x K]^T (+ bias, tanh, BF16 copy) on the tensor cores, A and B K-major
+int gemm_tc(rtbte_surrogate *s, const bf16 *A, int lda, const bf16 *B, int ldb, float *C, int ldc, int M, int N, int K,
+            const float *bias, int act, bf16 *Cb) {
+    const int bn_full = (N + 15) / 16 * 16;
+    const int bn = std::min(bn_full, 256);
+    CUtensorMap ta, tb;
+    if ((lda * (int)sizeof(bf16)) % 16 || (ldb * (int)sizeof(bf16)) % 16 || !kmajor_map(&ta, A, M, K, lda, umma::kTM) ||
+        !kmajor_map(&tb, B, N, K, ldb, bn))
+        return sfail(s, RTBTE_E_UNSUPPORTED, "tensor-core GEMM: operand layout not expressible as a TMA map");
+    umma::Args a;
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.bn = bn;
+    a.ldc = ldc;
+    a.act = act;
+    a.bias = bias;
+    a.C = C;
+    a.Cb = Cb;
+    a.err = s->tcerr.as<int>();
+    a.a_mn = a.b_mn = 0;
+    a.k_base = 0;
+    a.c_split = 0;
+    const dim3 grid((M + umma::kTM - 1) / umma::kTM, (N + bn - 1) / bn);
+    const size_t sm = umma::smem_bytes(bn);
+    cudaStream_t st = s->ctx->stream;
+    static bool attr_set = false;  // the shared-memory limit is a per-function attribute: set once
+    if (!attr_set) {
+        const void *fns[4] = {(const void *)umma::gemm_tc<32, 4>, (const void *)umma::gemm_tc<64, 4>,
+                              (const void *)umma::gemm_tc<128, 4>, (const void *)umma::gemm_tc<256, 2>};
+        for (const void *f : fns) S_CUDA(s, allow_max_dynamic_smem(f));
+        attr_set = true;
+    }
+    static_assert(umma::kTM * umma::kTK * 2 + 128 * umma::kTK * 2 <= 32768, "four stages for bn <= 128");
+    if (bn <= 32) umma::gemm_tc<32, 4><<<grid, umma::kThreads, sm, st>>>(ta, tb, a);
+    else if (bn <= 64) umma::gemm_tc<64, 4><<<grid, umma::kThreads, sm, st>>>(ta, tb, a);
+    else if (bn <= 128) umma::gemm_tc<128, 4><<<grid, umma::kThreads, sm, st>>>(ta, tb, a);
+    else umma::gemm_tc<256, 2><<<grid, umma::kThreads, sm, st>>>(ta, tb, a);
+    S_CUDA(s, cudaGetLastError());
+    s->ctx->launches++;
+    return RTBTE_OK;
+}
+
+// C[M x N] = A^T B on the tensor cores for A stored [K][M] (row stride lda) and B stored [K][N]
+// (row stride ldb), both MN-major, N a multiple of 64: K split over CTAs in multiples of 64, the
+// partial products summed in a fixed order (the weight gradients, a contraction over points)
+int gemm_tc_mn(rtbte_surrogate *s, const bf16 *A, int lda, const bf16 *B, int ldb, float *C, int ldc, int M, int N,
+               int K) {
+    if (N % 64 || N > 256) return sfail(s, RTBTE_E_UNSUPPORTED, "tensor-core GEMM: MN-major N must be 64..256 by 64");
+    CUtensorMap ta, tb;
+    if ((lda * (int)sizeof(bf16)) % 16 || (ldb * (int)sizeof(bf16)) % 16 || !kmajor_map(&ta, A, K, M, lda, 64) ||
+        !kmajor_map(&tb, B, K, N, ldb, 64))
+        return sfail(s, RTBTE_E_UNSUPPORTED, "tensor-core GEMM: operand layout not expressible as a TMA map");
+    const int mt = (M + umma::kTM - 1) / umma::kTM;
+    // about two CTAs per SM, at most 64 slices, each a whole number of 64-wide K slices
+    const int want = std::max(1, std::min(64, (2 * s->ctx->num_sms + mt - 1) / mt));
+    long long kc = ((long long)K + want - 1) / want;
+    kc = (kc + umma::kTK - 1) / umma::kTK * umma::kTK;
+    const int splits = (int)((K + kc - 1) / kc);
+    umma::Args a{};
+    a.M = M;
+    a.N = N;
+    a.K = (int)kc;
+    a.bn = N;
+    a.ldc = ldc;
+    a.act = 0;
+    a.C = splits > 1 ? s->split.as<float>() : C;
+    a.err = s->tcerr.as<int>();
+    a.a_mn = a.b_mn = 1;
+    a.k_base = 0;
+    a.c_split = (long long)M * ldc;
+    const dim3 grid(mt, 1, splits);
+    cudaStream_t st = s->ctx->stream;
+    if (N <= 64) umma::gemm_tc<64, 4><<<grid, umma::kThreads, umma::smem_bytes(64), st>>>(ta, tb, a);
+    else if (N <= 128) umma::gemm_tc<128, 4><<<grid, umma::kThreads, umma::smem_bytes(128), st>>>(ta, tb, a);
+    else umma::gemm_tc<256, 2><<<grid, umma::kThreads, umma::smem_bytes(N), st>>>(ta, tb, a);
+    S_CUDA(s, cudaGetLastError());
+    s->ctx->launches++;
+    if (splits > 1) {
+        sum_splits<<<blocks_for((long long)M * ldc), 256, 0, st>>>(s->split.as<float>(), splits, (long long)M * ldc, C);
+        S_CUDA(s, cudaGetLastError());
+        s->ctx->launches++;
+    }
+    return RTBTE_OK;
+}
+
+// K-major BF16 copies of the weights for the tensor-core forward GEMMs, refreshed after every
+// change of the master weights: W_l^T [w x kpad_l], M1^T [w x w], M2^T [C x w]
+int refresh_training_layout(rtbte_surrogate *s) {
+    if (s->engine != 0) return RTBTE_OK;
+    cudaStream_t st = s->ctx->stream;
+    bf16 *wt = s->wtt.as<bf16>();
+    const float *w = s->w.as<float>();
+    for (int l = 0; l < kLayers; ++l)
+        transpose_bf16<<<blocks_for((long long)s->kpad[l] * s->width), 256, 0, st>>>(w + s->off_W[l], s->kpad[l],
+                                                                                   s->width, wt + s->off_tt[l]);
+    transpose_bf16<<<blocks_for((long long)s->width * s->width), 256, 0, st>>>(w + s->off_M1, s->width, s->width,
+                                                                             wt + s->off_tt[kLayers]);
+    transpose_bf16<<<blocks_for((long long)s->width * s->C), 256, 0, st>>>(w + s->off_M2, s->width, s->C,
+                                                                         wt + s->off_tt[kLayers + 1]);
+    S_CUDA(s, cudaGetLastError());
+    s->ctx->launches += kLayers + 2;
+    return RTBTE_OK;
+}
+
+// the error word of the tensor-core GEMMs (a bounded wait that gave up); synchronises
+int check_tc(rtbte_surrogate *s) {
+    if (s->engine != 0) return RTBTE_OK;
+    int e = 0;
+    S_CUDA(s, cudaMemcpyAsync(&e, s->tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, s->ctx->stream));
+    S_CUDA(s, cudaStreamSynchronize(s->ctx->stream));
+    if (e) return sfail(s, RTBTE_E_TIMEOUT, "tensor-core GEMM: a bounded mbarrier wait gave up");
+    return RTBTE_OK;
+}
+
 // forward of B samples whose normalised input is in s->xb ([B*Pq][C] BF16); output FP32 in s->out
 int forward(rtbte_surrogate *s, int B) {
     cudaStream_t st = s->ctx->stream;
@@ -616,14 +771,27 @@ int forward(rtbte_surrogate *s, int B) {
         im2col<<<blocks_for(P * s->kpad[l]), 256, 0, st>>>(in, C, s->ny, s->nx, P, s->cols[l].as<bf16>(), s->kpad[l]);
         S_CUDA(s, cudaGetLastError());
         s->ctx->launches++;
-        if ((rc = gemm<false, false>(s, s->cols[l].as<bf16>(), s->kpad[l], s->wb.as<bf16>() + s->off_W[l], s->width,
-                                     s->acts[l + 1].as<float>(), s->width, (int)P, s->width, s->kpad[l],
-                                     s->w.as<float>() + s->off_b[l], 1, s->actb[l + 1].as<bf16>())))
-            return rc;
+        if (s->engine == 0)
+            rc = gemm_tc(s, s->cols[l].as<bf16>(), s->kpad[l], s->wtt.as<bf16>() + s->off_tt[l], s->kpad[l],
+                         s->acts[l + 1].as<float>(), s->width, (int)P, s->width, s->kpad[l],
+                         s->w.as<float>() + s->off_b[l], 1, s->actb[l + 1].as<bf16>());
+        else
+            rc = gemm<false, false>(s, s->cols[l].as<bf16>(), s->kpad[l], s->wb.as<bf16>() + s->off_W[l], s->width,
+                                    s->acts[l + 1].as<float>(), s->width, (int)P, s->width, s->kpad[l],
+                                    s->w.as<float>() + s->off_b[l], 1, s->actb[l + 1].as<bf16>());
+        if (rc) return rc;
         in = s->actb[l + 1].as<bf16>();
         C = s->width;
     }
     // pointwise MLP: h5 = tanh(h4 M1 + c1) (reuses acts[0]), out = h5 M2 + c2
+    if (s->engine == 0) {
+        if ((rc = gemm_tc(s, s->actb[kLayers].as<bf16>(), s->width, s->wtt.as<bf16>() + s->off_tt[kLayers], s->width,
+                          s->acts[0].as<float>(), s->width, (int)P, s->width, s->width, s->w.as<float>() + s->off_c1, 1,
+                          s->actb[0].as<bf16>())))
+            return rc;
+        return gemm_tc(s, s->actb[0].as<bf16>(), s->width, s->wtt.as<bf16>() + s->off_tt[kLayers + 1], s->width,
+                       s->out.as<float>(), s->C, (int)P, s->C, s->width, s->w.as<float>() + s->off_c2, 0, nullptr);
+    }
     if ((rc = gemm<false, false>(s, s->actb[kLayers].as<bf16>(), s->width, s->wb.as<bf16>() + s->off_M1, s->width,
                                  s->acts[0].as<float>(), s->width, (int)P, s->width, s->width,
                                  s->w.as<float>() + s->off_c1, 1, s->actb[0].as<bf16>())))
@@ -662,27 +830,43 @@ int loss_grad(rtbte_surrogate *s, int B, float *loss, bool diff = false) {
         return rc;
     tanh_back<<<blocks_for(P * Wd), 256, 0, st>>>(s->ga.as<float>(), s->acts[0].as<float>(), P * Wd, s->gz.as<float>(),
                                                    s->gzb.as<bf16>());
-    if ((rc = gemm<true, false>(s, s->actb[kLayers].as<bf16>(), Wd, s->gzb.as<bf16>(), Wd, g + s->off_M1, Wd, Wd, Wd,
-                                (int)P, nullptr, 0, nullptr, splitsP)))
-        return rc;
+    const bool tc_mn = s->engine == 0 && Wd % 64 == 0;  // weight gradients on the tensor cores (MN-major operands)
+    if (tc_mn)
+        rc = gemm_tc_mn(s, s->actb[kLayers].as<bf16>(), Wd, s->gzb.as<bf16>(), Wd, g + s->off_M1, Wd, Wd, Wd, (int)P);
+    else
+        rc = gemm<true, false>(s, s->actb[kLayers].as<bf16>(), Wd, s->gzb.as<bf16>(), Wd, g + s->off_M1, Wd, Wd, Wd,
+                               (int)P, nullptr, 0, nullptr, splitsP);
+    if (rc) return rc;
     col_sums<<<Wd, 256, 0, st>>>(s->gz.as<float>(), P, Wd, g + s->off_c1);
-    // g_h4 = gz5 M1^T
-    if ((rc = gemm<false, true>(s, s->gzb.as<bf16>(), Wd, s->wb.as<bf16>() + s->off_M1, Wd, s->ga.as<float>(), Wd,
-                                (int)P, Wd, Wd, nullptr, 0, nullptr)))
-        return rc;
+    // g_h4 = gz5 M1^T (M1 itself is the K-major [n][k] operand)
+    if (s->engine == 0)
+        rc = gemm_tc(s, s->gzb.as<bf16>(), Wd, s->wb.as<bf16>() + s->off_M1, Wd, s->ga.as<float>(), Wd, (int)P, Wd, Wd,
+                     nullptr, 0, nullptr);
+    else
+        rc = gemm<false, true>(s, s->gzb.as<bf16>(), Wd, s->wb.as<bf16>() + s->off_M1, Wd, s->ga.as<float>(), Wd,
+                               (int)P, Wd, Wd, nullptr, 0, nullptr);
+    if (rc) return rc;
     for (int l = kLayers - 1; l >= 0; --l) {
         tanh_back<<<blocks_for(P * Wd), 256, 0, st>>>(s->ga.as<float>(), s->acts[l + 1].as<float>(), P * Wd,
                                                        s->gz.as<float>(), s->gzb.as<bf16>());
         // dW_l = cols_l^T gz  ([kpad x Wd]); the rows beyond 9*C_in stay zero
-        if ((rc = gemm<true, false>(s, s->cols[l].as<bf16>(), s->kpad[l], s->gzb.as<bf16>(), Wd, g + s->off_W[l], Wd,
-                                    s->kpad[l], Wd, (int)P, nullptr, 0, nullptr, splitsP)))
-            return rc;
+        if (tc_mn)
+            rc = gemm_tc_mn(s, s->cols[l].as<bf16>(), s->kpad[l], s->gzb.as<bf16>(), Wd, g + s->off_W[l], Wd,
+                            s->kpad[l], Wd, (int)P);
+        else
+            rc = gemm<true, false>(s, s->cols[l].as<bf16>(), s->kpad[l], s->gzb.as<bf16>(), Wd, g + s->off_W[l], Wd,
+                                   s->kpad[l], Wd, (int)P, nullptr, 0, nullptr, splitsP);
+        if (rc) return rc;
         col_sums<<<Wd, 256, 0, st>>>(s->gz.as<float>(), P, Wd, g + s->off_b[l]);
         if (l == 0) break;
         // gcol = gz W_l^T  ([P x kpad]), then col2im into the previous activation's gradient
-        if ((rc = gemm<false, true>(s, s->gzb.as<bf16>(), Wd, s->wb.as<bf16>() + s->off_W[l], Wd,
-                                    s->gcol.as<float>(), s->kpad[l], (int)P, s->kpad[l], Wd, nullptr, 0, nullptr)))
-            return rc;
+        if (s->engine == 0)
+            rc = gemm_tc(s, s->gzb.as<bf16>(), Wd, s->wb.as<bf16>() + s->off_W[l], Wd, s->gcol.as<float>(), s->kpad[l],
+                         (int)P, s->kpad[l], Wd, nullptr, 0, nullptr);
+        else
+            rc = gemm<false, true>(s, s->gzb.as<bf16>(), Wd, s->wb.as<bf16>() + s->off_W[l], Wd, s->gcol.as<float>(),
+                                   s->kpad[l], (int)P, s->kpad[l], Wd, nullptr, 0, nullptr);
+        if (rc) return rc;
         col2im<<<blocks_for(P * s->cin[l]), 256, 0, st>>>(s->gcol.as<float>(), s->cin[l], s->ny, s->nx, P, s->kpad[l],
                                                           s->ga.as<float>());
     }
@@ -1006,6 +1190,24 @@ int rtbte_surrogate_create(rtbte_ctx *ctx, int inst, int width, int capacity, ui
     if (cudaMemcpy(s->w.p, w.data(), sizeof(float) * off, cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(RTBTE_E_CUDA);
     to_bf16<<<blocks_for(off), 256, 0, ctx->stream>>>(s->w.as<float>(), off, s->wb.as<bf16>());
+    // tensor-core GEMMs (tcgen05) when the device has them and TMA maps can be made
+    {
+        int cc = 0;
+        cudaDeviceGetAttribute(&cc, cudaDevAttrComputeCapabilityMajor, ctx->device);
+        s->engine = (cc >= 10 && encode_tiled()) ? 0 : 1;
+        long long t = 0;
+        for (int l = 0; l < kLayers; ++l) {
+            s->off_tt[l] = t;
+            t += (long long)s->kpad[l] * width;
+        }
+        s->off_tt[kLayers] = t;
+        t += (long long)width * width;
+        s->off_tt[kLayers + 1] = t;
+        t += (long long)width * s->C;
+        if ((rc = salloc(s, s->wtt, sizeof(bf16) * t)) || (rc = salloc(s, s->tcerr, sizeof(int)))) return bail(rc);
+        cudaMemset(s->tcerr.p, 0, sizeof(int));
+        if ((rc = refresh_training_layout(s))) return bail(rc);
+    }
     s->fused = width == kIW;
     if (s->fused) {
         long long t = 0;
@@ -1122,9 +1324,11 @@ int rtbte_surrogate_train(rtbte_surrogate *s, int steps, int batch, int horizon,
             1.f - powf(b1, (float)s->adam_t), 1.f - powf(b2, (float)s->adam_t), s->wb.as<bf16>());
         S_CUDA(s, cudaGetLastError());
         ctx->launches++;
+        if ((rc = refresh_training_layout(s))) return rc;
     }
     if ((rc = refresh_inference(s))) return rc;
     S_CUDA(s, cudaStreamSynchronize(ctx->stream));
+    if ((rc = check_tc(s))) return rc;
     if (loss_out) *loss_out = last;
     return RTBTE_OK;
 }
@@ -1161,7 +1365,22 @@ int rtbte_surrogate_set_params(rtbte_surrogate *s, const float *host) {
     if (!s || !host) return RTBTE_E_INVALID_ARG;
     if (!s->ctx) return sfail(s, RTBTE_E_STATE, "context destroyed");
     int rc = params_io(s, const_cast<float *>(host), true);
-    if (rc || (rc = refresh_inference(s))) return rc;
+    if (rc || (rc = refresh_inference(s)) || (rc = refresh_training_layout(s))) return rc;
+    S_CUDA(s, cudaStreamSynchronize(s->ctx->stream));
+    return RTBTE_OK;
+}
+
+int rtbte_surrogate_set_gemm(rtbte_surrogate *s, int engine) {
+    if (!s || engine < 0 || engine > 1) return RTBTE_E_INVALID_ARG;
+    if (!s->ctx) return sfail(s, RTBTE_E_STATE, "context destroyed");
+    if (engine == 0) {
+        int cc = 0;
+        cudaDeviceGetAttribute(&cc, cudaDevAttrComputeCapabilityMajor, s->ctx->device);
+        if (cc < 10 || !encode_tiled()) return sfail(s, RTBTE_E_UNSUPPORTED, "no tcgen05 tensor cores or TMA maps");
+    }
+    s->engine = engine;
+    int rc;
+    if ((rc = refresh_training_layout(s))) return rc;
     S_CUDA(s, cudaStreamSynchronize(s->ctx->stream));
     return RTBTE_OK;
 }
@@ -1177,7 +1396,7 @@ int rtbte_surrogate_loss_grad(rtbte_surrogate *s, const float *x, const float *t
     for (long long i = 0; i < n; ++i) xb[i] = __float2bfloat16(x[i]);
     S_CUDA(s, cudaMemcpy(s->xb.p, xb.data(), sizeof(bf16) * n, cudaMemcpyHostToDevice));
     S_CUDA(s, cudaMemcpy(s->t.p, t, sizeof(float) * n, cudaMemcpyHostToDevice));
-    if ((rc = loss_grad(s, B, loss))) return rc;
+    if ((rc = loss_grad(s, B, loss)) || (rc = check_tc(s))) return rc;
     if (out) S_CUDA(s, cudaMemcpy(out, s->out.p, sizeof(float) * n, cudaMemcpyDeviceToHost));
     if (grad) {
         // gradients in the logical layout
@@ -1212,7 +1431,7 @@ void rtbte_surrogate_destroy(rtbte_surrogate *s) {
     DevBuf *bufs[] = {&s->w,  &s->wb,  &s->g,     &s->m,    &s->v,     &s->stats, &s->ppfull, &s->Ns,
                       &s->Is, &s->idx, &s->xb,    &s->t,    &s->out,   &s->gout,  &s->goutb,  &s->ga,
                       &s->gz, &s->gzb, &s->gcol,  &s->split, &s->lossp, &s->ydot, &s->Eref,   &s->out_ref,
-                      &s->normp, &s->wbt, &s->a0,  &s->a1};
+                      &s->normp, &s->wbt, &s->a0,  &s->a1, &s->wtt, &s->tcerr};
     for (DevBuf *b : bufs) b->release();
     for (int l = 0; l < kLayers; ++l) s->cols[l].release();
     for (int l = 0; l <= kLayers; ++l) {

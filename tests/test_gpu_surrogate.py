@@ -86,6 +86,31 @@ def test_loss_and_gradients_match_fp64_oracle(rt, g36, width, B):
     s.close()
 
 
+@pytest.mark.parametrize("width,B", [(64, 3), (24, 16), (64, 40)])
+def test_tensor_core_engine_matches_mma_sync(rt, g36, width, B):
+    """The default GEMM engine on this GPU is the tcgen05 one (forward layers and input gradients
+    on the fifth-generation tensor cores, TMA-fed, accumulators in tensor memory).  On the same
+    weights and inputs its output, loss and gradients agree with the mma.sync engine to FP32
+    accumulation-order rounding; the sizes give ragged M tiles (3 x 144 and 40 x 144 points), N
+    below 16 (the 6 output channels), N tiles of 256 + 256 + 64 (576-column input gradients)
+    and N 24 / K 24 (width 24)."""
+    m, ctx = g36
+    s = rt.Surrogate(ctx, width=width, capacity=1, seed=9)
+    rng = np.random.default_rng(7 * width + B)
+    ny, nx = s.nq_s[1], s.nq_s[0]
+    x = rng.standard_normal((B, ny, nx, m.nmodes)).astype(np.float32)
+    t = (0.3 * rng.standard_normal((B, ny, nx, m.nmodes))).astype(np.float32)
+    res = []
+    for engine in (0, 1):
+        s.set_gemm(engine)
+        res.append(s.loss_grad(x, t))
+    (l0, g0, o0), (l1, g1, o1) = res
+    assert relL2(o0, o1) < 1e-5
+    assert abs(l0 - l1) < 1e-5 * l1
+    assert relL2(g0, g1) < 1e-4
+    s.close()
+
+
 def trajectory_states(rt, m, ctx, n_traj=4, per=6, t_end=0.06):
     """(device state, trajectory id) along the method's own trajectories from several initial
     conditions (excitation energy, amplitude, temperature) on the same channels."""

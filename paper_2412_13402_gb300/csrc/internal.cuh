@@ -38,7 +38,7 @@ constexpr int kWrmsChunks = 128;  // per-instance blocks of the WRMS reduction b
 constexpr int kLoopCap = 64;     // attempts per launch of an attempt-loop graph (default)
 
 enum { PART_EPH = 0, PART_PHE = 1, PART_PP = 2 };
-// Lanes working on one item are chosen per staging group (Group::lanes_log2): 8, 16 or 32 lanes,
+// Lanes working on one item are chosen per staging group (Group::lanes_log2): 4, 8, 16 or 32 lanes,
 // items of at most 16 x lanes entries, so that groups of short segments pack several items into
 // one warp while groups of long segments keep whole-warp items.
 
@@ -58,7 +58,7 @@ struct __align__(16) Group {
     int item_begin, item_end;
     int part, inst, nu, s_bits;
     int pp_bits, n_q_pad;
-    int lanes_log2, pad_g;       // lanes per item = 1 << lanes_log2 (3, 4 or 5)
+    int lanes_log2, pad_g;       // lanes per item = 1 << lanes_log2 (2, 3, 4 or 5)
     int stage0_len, stage1_len;  // staged element counts (multiples of 4)
     int stage1_q0, pad_s;        // e-ph: first q of the staged block of the mode's N
     long long stage0_src;        // popf (e-ph, ph-e) or popP (ph-ph) offset of the staged block

@@ -8,8 +8,8 @@
 // whole mode does not fit (the e-ph lists are blocked by mode and block for this reason); for
 // ph-e work only f; for ph-ph work the sub-lattice N.  A work item is a piece
 // of a single destination segment; groups of long segments give each warp one item of up to
-// 512 entries, groups of short ones give each sub-warp of 8 or 16 lanes one item of up to 128
-// or 256 entries.  Lanes accumulate their entries with
+// 512 entries, groups of short ones give each sub-warp of 4, 8 or 16 lanes one item of up to 64,
+// 128 or 256 entries.  Lanes accumulate their entries with
 // compensated (two-sum) additions and adds the lanes with a shuffle tree; the partial is
 // written per item, and the row kernels add partials in item order (deterministic).  CTAs
 // first run a static share of the items (split by estimated cost), then take the rest in
@@ -748,7 +748,7 @@ int make_plan(rtbte_ctx *ctx) {
                 ++n;
             }
         const double mean = n ? (double)tot / (double)n : 0.0;
-        return mean <= 128.0 ? 3 : mean <= 256.0 ? 4 : 5;
+        return mean <= 64.0 ? 2 : mean <= 128.0 ? 3 : mean <= 256.0 ? 4 : 5;
     };
     auto add_seg = [&](long long b, long long e, int dest, int proc) {
         for (long long x = b; x < e; x += cut) {

@@ -845,11 +845,11 @@ def graphene_long_study(rt, ri, dev, t_end=100.0, window=5.0):
     return out
 
 
-def silicon_long_study(rt, ri, dev, t_end=20.0, window=1.0):
-    """Config 3's integration length at the printed grids: MRI (h_s = 50 fs, the silicon tolerances of Methods A)
-    with FP32 compensated sums to t_end in windows (controller resumed across windows), with
-    the mean excess energy of the carriers and the phonon energy per window; FP64 over the
-    first window for the precision comparison at that time."""
+def silicon_long_study(rt, ri, dev, t_end=20.0, window=1.0, fp64_t_end=None):
+    """Config 3's integration length at the printed grids: MRI (h_s = 50 fs, the silicon tolerances of
+    Methods A) to t_end in windows (controller resumed across windows), once with FP32 compensated sums
+    and once with FP64 sums everywhere (to fp64_t_end, default t_end), with the mean excess energy of the
+    carriers, the phonon energy and the FP32-vs-FP64 population difference per window."""
     import numpy as np
     import torch
 
@@ -859,54 +859,54 @@ def silicon_long_study(rt, ri, dev, t_end=20.0, window=1.0):
     om = np.asarray(m.ph_omega)
     nq = float(np.prod(m.nq))
     tol = dict(rtol=1e-5, atol_c=1e-9, atol_ph=1e-11)
+    fp64_t_end = t_end if fp64_t_end is None else min(fp64_t_end, t_end)
 
     def observables(y):
         f, N = y[:nc], y[nc:]
         return {"carrier_mean_energy_eV": float((eps * f).sum() / f.sum()),
                 "phonon_energy_eV_per_cell": float((om * N).sum() / nq)}
 
+    def integrate(precision, t_stop):
+        c = rt.Context(m, precision=precision, device=dev.index or 0)
+        c.upload_channels()
+        y = torch.tensor(m.y0(), device=dev)
+        c.rhs(y, torch.empty_like(y))
+        c.autotune(rt.RTBTE_ALL)
+        wins, states, t = [], [], 0.0
+        while t < t_stop - 1e-12:
+            t1 = min(t + window, t_stop)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(c.stream)
+            st = c.advance_to(t1, y, method="mri", t0=t, h_s=0.050, resume=1 if t > 0 else 0, **tol)
+            e1.record(c.stream)
+            torch.cuda.synchronize()
+            assert st["status"] == 0, st
+            yh = y.cpu().numpy()
+            states.append(yh.copy())
+            wins.append({"t_ps": t1, "seconds": e0.elapsed_time(e1) / 1000.0, "fast_steps": st["steps"],
+                         "slow_steps": st["slow_steps"], "rhs_fast": st["rhs_fast"], "rhs_slow": st["rhs_slow"],
+                         **observables(yh)})
+            t = t1
+        c.close()
+        return wins, states
+
     out = {"workload": "silicon-like 3D at the printed grids (80^3 / 40^3, ph-ph on the stride-2 sub-lattice)",
-           "method": "MRI h_s 50 fs, rtol 1e-5, atol_c 1e-9, atol_ph 1e-11", "t_end_ps": t_end, "window_ps": window}
-    c = rt.Context(m, precision="fp32", device=dev.index or 0)
-    c.upload_channels()
-    y = torch.tensor(m.y0(), device=dev)
-    c.rhs(y, torch.empty_like(y))
-    c.autotune(rt.RTBTE_ALL)
-    wins, t, y1 = [], 0.0, None
-    obs0 = observables(m.y0())
-    while t < t_end - 1e-12:
-        t1 = min(t + window, t_end)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(c.stream)
-        st = c.advance_to(t1, y, method="mri", t0=t, h_s=0.050, resume=1 if t > 0 else 0, **tol)
-        e1.record(c.stream)
-        torch.cuda.synchronize()
-        assert st["status"] == 0, st
-        yh = y.cpu().numpy()
-        if y1 is None:
-            y1 = yh.copy()
-        wins.append({"t_ps": t1, "seconds": e0.elapsed_time(e1) / 1000.0, "fast_steps": st["steps"],
-                     "slow_steps": st["slow_steps"], "rhs_fast": st["rhs_fast"], "rhs_slow": st["rhs_slow"],
-                     **observables(yh)})
-        t = t1
-    c.close()
-    total = sum(w["seconds"] for w in wins)
-    out.update({"initial": obs0, "windows": wins, "seconds": total, "sim_ps_per_s": t_end / total})
-    c = rt.Context(m, precision="fp64", device=dev.index or 0)
-    c.upload_channels()
-    y = torch.tensor(m.y0(), device=dev)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(c.stream)
-    st = c.advance_to(window, y, method="mri", t0=0.0, h_s=0.050, **tol)
-    e1.record(c.stream)
-    torch.cuda.synchronize()
-    y64 = y.cpu().numpy()
-    c.close()
-    out["fp64_first_window"] = {"status": st["status"], "seconds": e0.elapsed_time(e1) / 1000.0,
-                                "fp32_vs_fp64_carriers": float(np.linalg.norm(y1[:nc] - y64[:nc]) / np.linalg.norm(y64[:nc])),
-                                "fp32_vs_fp64_phonons": float(np.linalg.norm(y1[nc:] - y64[nc:]) / np.linalg.norm(y64[nc:]))}
+           "method": "MRI h_s 50 fs, rtol 1e-5, atol_c 1e-9, atol_ph 1e-11", "t_end_ps": t_end, "window_ps": window,
+           "initial": observables(m.y0())}
+    w32, s32 = integrate("fp32", t_end)
+    sec32 = sum(w["seconds"] for w in w32)
+    out["fp32"] = {"windows": w32, "seconds": sec32, "sim_ps_per_s": t_end / sec32}
+    w64, s64 = integrate("fp64", fp64_t_end)
+    for w, a, b in zip(w64, s32, s64):
+        w["fp32_vs_fp64_carriers"] = float(np.linalg.norm(a[:nc] - b[:nc]) / np.linalg.norm(b[:nc]))
+        w["fp32_vs_fp64_phonons"] = float(np.linalg.norm(a[nc:] - b[nc:]) / np.linalg.norm(b[nc:]))
+        w["fp32_vs_fp64_max_rel"] = float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+    sec64 = sum(w["seconds"] for w in w64)
+    out["fp64"] = {"windows": w64, "seconds": sec64, "sim_ps_per_s": fp64_t_end / sec64,
+                   "t_end_ps": fp64_t_end, "fp32_speedup": (t_end / sec32) / (fp64_t_end / sec64)}
+    out["max_fp32_vs_fp64"] = {"carriers": max(w["fp32_vs_fp64_carriers"] for w in w64),
+                               "phonons": max(w["fp32_vs_fp64_phonons"] for w in w64)}
     return out
 
 

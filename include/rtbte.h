@@ -325,8 +325,10 @@ int rtbte_set_stream(rtbte_ctx *ctx, void *stream);
  * entry equivalents and c_part the calibrated cost of an entry of each part; a share s of the
  * weight is split statically, the rest is taken in chunks by CTAs that finish early; each
  * warp prefetches the entry arrays of the item d positions ahead of its sequence into L2.
- * This call times the kernel for `parts` over candidates of w, c_part, d and s and keeps the
- * fastest (w in *chosen when not NULL).  Synchronises the stream; results of later calls do
+ * In FP32 the kernel also has two launch forms, two register buffers of entries per warp at 16
+ * warps per SM or one buffer at 24 warps per SM, chosen per parts mask.
+ * This call times the kernel for `parts` over the forms and candidates of w, c_part, d and s and
+ * keeps the fastest (w in *chosen when not NULL).  Synchronises the stream; results of later calls do
  * not depend on the choice (rows add item partials in a fixed order).
  * Errors: INVALID_ARG, STATE, CUDA. */
 int rtbte_autotune(rtbte_ctx *ctx, unsigned parts, int *chosen);

@@ -30,7 +30,8 @@ namespace rtbte {
 
 constexpr int kItemEntries = 512;  // 32 lanes x 4 vectors x 4 entries
 constexpr int kSegPad = 4;
-constexpr int kRhsThreads = 512;
+constexpr int kRhsThreads = 512;      // collision kernel, threads per SM: two register buffers of entries per warp
+constexpr int kRhsThreadsDeep = 768;  // FP32 single-buffer form: 24 warps per SM at 80 registers
 constexpr int kMaxModes = 16;
 constexpr int kMaxStages = 5;
 constexpr int kWrmsBlocks = 512;
@@ -219,7 +220,9 @@ struct rtbte_ctx {
     int n_items = 0, n_groups = 0;
     int part_items[3] = {0, 0, 0};
     int part_first[3] = {0, 0, 0};
-    int grid = 0, threads = rtbte::kRhsThreads;
+    int grid = 0, per_sm = 1;  // collision kernel: CTAs per SM (1, 2 or 4; threads = form's threads per SM / per_sm)
+    bool deep[8] = {};         // FP32 launches of parts mask m use the single-buffer 768-thread form
+    unsigned deep_tuned = 0;   // masks whose form the autotuner chose (kept across plans)
     std::vector<unsigned short> item_len_h;  // entries per work item (host copy for re-splitting)
     std::vector<int> group_begin_h;          // first item of each group (host copy)
     int item_overhead = 320;                 // work-split weight of an item beyond its entries

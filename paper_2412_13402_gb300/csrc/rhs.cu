@@ -13,7 +13,10 @@
 // compensated (two-sum) additions and adds the lanes with a shuffle tree; the partial is
 // written per item, and the row kernels add partials in item order (deterministic).  CTAs
 // first run a static share of the items (split by estimated cost), then take the rest in
-// chunks from a counter; warps may prefetch upcoming items' entries into L2.
+// chunks from a counter; warps may prefetch upcoming items' entries into L2.  FP32 launches
+// come in two forms, chosen per parts mask: two register buffers of entries per warp (the next
+// item's loads in flight during the current one's arithmetic) at 16 warps per SM, or one buffer
+// at 24 warps per SM.
 //
 // Per-entry arithmetic uses the exact algebraic reductions of the paper's factors
 // (Methods A):  F_em = f(1-f') + N(f-f'),  F_abs = N(f-f') - f'(1-f),
@@ -433,8 +436,8 @@ __device__ __forceinline__ void enter_group(const KParams &P, int g, R *sm, int 
 // counter until none is left, so that SMs that finish early absorb the tail of the work.
 // Items are round-robin over the warps of the CTA; every item writes its own partial, so the
 // result does not depend on which CTA ran it.
-template <class R, bool STAGED, bool PIPE, bool WIDE, int MINB>
-__global__ void __launch_bounds__(kRhsThreads, MINB) rhs_kernel(KParams P) {
+template <class R, bool STAGED, bool PIPE, bool WIDE, int MINB, int NT>
+__global__ void __launch_bounds__(NT, MINB) rhs_kernel(KParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_chunk;
     R *sm = reinterpret_cast<R *>(smem_raw);
@@ -898,29 +901,45 @@ int make_plan(rtbte_ctx *ctx) {
     // overlaps the others' streaming
     ctx->staged = max_stage + 64 <= ctx->smem_optin;  // 64 B left for the kernel's static shared memory
     ctx->smem_bytes = ctx->staged ? std::max<size_t>(max_stage, 16) : 0;
+    // Two forms of the FP32 kernel: two register buffers of entries per warp at 16 warps per SM
+    // (128 registers), or one buffer at 24 warps per SM (80 registers), which hides the gather and
+    // arithmetic latency better on the e-ph part.  Both must fit the chosen CTAs per SM.
     int per_sm = 1;
-    ctx->threads = kRhsThreads;
+    const bool fp64 = ctx->precision == RTBTE_PREC_FP64;
     if (ctx->staged) {
-        const bool fp64 = ctx->precision == RTBTE_PREC_FP64;
-        const void *kfns[2] = {fp64 ? (const void *)rhs_kernel<double, true, false, true, 1>
-                                    : (const void *)rhs_kernel<float, true, true, true, 1>,
-                               fp64 ? (const void *)rhs_kernel<double, true, false, false, 1>
-                                    : (const void *)rhs_kernel<float, true, true, false, 1>};
-        for (const void *f : kfns) {
-            RT_CUDA(ctx, allow_max_dynamic_smem(f));
-            RT_CUDA(ctx, cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        std::vector<std::pair<const void *, int>> kfns;  // (kernel, threads per SM)
+        if (fp64) {
+            kfns.push_back({ctx->wide ? (const void *)rhs_kernel<double, true, false, true, 1, kRhsThreads>
+                                      : (const void *)rhs_kernel<double, true, false, false, 1, kRhsThreads>,
+                            kRhsThreads});
+        } else {
+            kfns.push_back({ctx->wide ? (const void *)rhs_kernel<float, true, true, true, 1, kRhsThreads>
+                                      : (const void *)rhs_kernel<float, true, true, false, 1, kRhsThreads>,
+                            kRhsThreads});
+            kfns.push_back({ctx->wide ? (const void *)rhs_kernel<float, true, false, true, 1, kRhsThreadsDeep>
+                                      : (const void *)rhs_kernel<float, true, false, false, 1, kRhsThreadsDeep>,
+                            kRhsThreadsDeep});
         }
-        const void *kfn = kfns[ctx->wide ? 0 : 1];
+        for (auto &kf : kfns) {
+            RT_CUDA(ctx, allow_max_dynamic_smem(kf.first));
+            RT_CUDA(ctx, cudaFuncSetAttribute(kf.first, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        }
         for (int k : {4, 2}) {
-            int nb = 0;
-            RT_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, kRhsThreads / k, ctx->smem_bytes));
-            if (nb >= k) {
+            bool fits = true;
+            for (auto &kf : kfns) {
+                int nb = 0;
+                RT_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kf.first, kf.second / k, ctx->smem_bytes));
+                fits = fits && nb >= k;
+            }
+            if (fits) {
                 per_sm = k;
                 break;
             }
         }
-        ctx->threads = kRhsThreads / per_sm;
     }
+    ctx->per_sm = per_sm;
+    for (unsigned m = 0; m < 8; ++m)  // default: the 768-thread form where e-ph work is in the launch
+        if (!(ctx->deep_tuned & (1u << m))) ctx->deep[m] = !fp64 && (m & (1u << PART_EPH));
     ctx->grid = ctx->num_sms * (ctx->staged ? per_sm : 2);
     ctx->item_len_h.resize(items.size());
     for (size_t k = 0; k < items.size(); ++k) ctx->item_len_h[k] = items[k].len;
@@ -1024,13 +1043,28 @@ static int launch_core_t(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStr
             RT_CUDA(ctx, cudaEventRecord(e0, s));
         }
     }
-    if (ctx->staged) {
-        if (ctx->wide)
-            rhs_kernel<R, true, sizeof(R) == 4, true, 1><<<ctx->grid, ctx->threads, ctx->smem_bytes, s>>>(P);
-        else
-            rhs_kernel<R, true, sizeof(R) == 4, false, 1><<<ctx->grid, ctx->threads, ctx->smem_bytes, s>>>(P);
+    if (!ctx->staged) {
+        rhs_kernel<R, false, false, false, 2, kRhsThreads><<<ctx->grid, kRhsThreads, 0, s>>>(P);
+    } else if constexpr (sizeof(R) == 4) {
+        if (ctx->deep[parts]) {
+            const int nt = kRhsThreadsDeep / ctx->per_sm;
+            if (ctx->wide)
+                rhs_kernel<R, true, false, true, 1, kRhsThreadsDeep><<<ctx->grid, nt, ctx->smem_bytes, s>>>(P);
+            else
+                rhs_kernel<R, true, false, false, 1, kRhsThreadsDeep><<<ctx->grid, nt, ctx->smem_bytes, s>>>(P);
+        } else {
+            const int nt = kRhsThreads / ctx->per_sm;
+            if (ctx->wide)
+                rhs_kernel<R, true, true, true, 1, kRhsThreads><<<ctx->grid, nt, ctx->smem_bytes, s>>>(P);
+            else
+                rhs_kernel<R, true, true, false, 1, kRhsThreads><<<ctx->grid, nt, ctx->smem_bytes, s>>>(P);
+        }
     } else {
-        rhs_kernel<R, false, false, false, 2><<<ctx->grid, ctx->threads, 0, s>>>(P);
+        const int nt = kRhsThreads / ctx->per_sm;
+        if (ctx->wide)
+            rhs_kernel<R, true, false, true, 1, kRhsThreads><<<ctx->grid, nt, ctx->smem_bytes, s>>>(P);
+        else
+            rhs_kernel<R, true, false, false, 1, kRhsThreads><<<ctx->grid, nt, ctx->smem_bytes, s>>>(P);
     }
     RT_CUDA(ctx, cudaGetLastError());
     ctx->launches++;
@@ -1047,34 +1081,34 @@ int launch_rhs_core(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStream_t
                                              : launch_core_t<float>(ctx, parts, ctl, s);
 }
 
-// Autotuner of the work split: time the collision kernel with each candidate per-item weight
-// and keep the fastest.
-int autotune(rtbte_ctx *ctx, unsigned parts, int *chosen) {
+namespace {
+
+// Time `reps` collision launches for `parts` after one untimed launch.
+int time_launches(rtbte_ctx *ctx, unsigned parts, cudaEvent_t e0, cudaEvent_t e1, int reps, float *ms) {
+    int rc;
+    if ((rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) return rc;
+    RT_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+    for (int r = 0; r < reps; ++r)
+        if ((rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) return rc;
+    RT_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+    RT_CUDA(ctx, cudaEventSynchronize(e1));
+    RT_CUDA(ctx, cudaEventElapsedTime(ms, e0, e1));
+    return RTBTE_OK;
+}
+
+// Tuning of the work split for the current kernel form: per-item weight, per-part entry costs,
+// L2 prefetch distance and static share, each timed over 3 launches and the fastest kept.
+int tune_split(rtbte_ctx *ctx, unsigned parts, cudaEvent_t e0, cudaEvent_t e1, int *chosen) {
     static const int cand[] = {32, 96, 192, 320, 512, 800, 1280, 2048};
-    cudaEvent_t e0, e1;
-    RT_CUDA(ctx, cudaEventCreate(&e0));
-    RT_CUDA(ctx, cudaEventCreate(&e1));
     int best = ctx->item_overhead, rc = RTBTE_OK;
     float best_ms = 1e30f;
     for (int w : cand) {
-        if ((rc = split_tables(ctx, w))) break;
-        if ((rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) break;
-        RT_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-        for (int r = 0; r < 3 && !rc; ++r) rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream);
-        if (rc) break;
-        RT_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
-        RT_CUDA(ctx, cudaEventSynchronize(e1));
         float ms = 0.f;
-        RT_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        if ((rc = split_tables(ctx, w)) || (rc = time_launches(ctx, parts, e0, e1, 3, &ms))) return rc;
         if (ms < best_ms) {
             best_ms = ms;
             best = w;
         }
-    }
-    if (rc) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return rc;
     }
     if ((rc = split_tables(ctx, best))) return rc;
     // calibrate the relative cost of an entry in each part from single-part launches, keep it
@@ -1082,23 +1116,16 @@ int autotune(rtbte_ctx *ctx, unsigned parts, int *chosen) {
     const double scale0[3] = {ctx->part_scale[0], ctx->part_scale[1], ctx->part_scale[2]};
     double t[3] = {0, 0, 0}, wsum[3] = {0, 0, 0};
     int used = 0;
-    for (int part = 0; part < 3 && !rc; ++part) {
+    for (int part = 0; part < 3; ++part) {
         if (!(parts & (1u << part)) || ctx->part_items[part] == 0) continue;
         for (int k = ctx->part_first[part]; k < ctx->part_first[part] + ctx->part_items[part]; ++k)
             wsum[part] += ctx->item_len_h[k] + best;
-        const unsigned pm = 1u << part;
-        if ((rc = launch_rhs_core(ctx, pm, nullptr, ctx->stream))) break;
-        RT_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-        for (int r = 0; r < 3 && !rc; ++r) rc = launch_rhs_core(ctx, pm, nullptr, ctx->stream);
-        if (rc) break;
-        RT_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
-        RT_CUDA(ctx, cudaEventSynchronize(e1));
         float ms = 0.f;
-        RT_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        if ((rc = time_launches(ctx, 1u << part, e0, e1, 3, &ms))) return rc;
         t[part] = ms;
-        used |= pm;
+        used |= 1u << part;
     }
-    if (!rc && used) {
+    if (used) {
         double ref = 0.0;
         int nref = 0;
         for (int part = 0; part < 3; ++part)
@@ -1109,69 +1136,98 @@ int autotune(rtbte_ctx *ctx, unsigned parts, int *chosen) {
         ref /= nref;
         for (int part = 0; part < 3; ++part)
             if (used & (1u << part)) ctx->part_scale[part] = (t[part] / wsum[part]) / ref;
-        if (!(rc = split_tables(ctx, best))) {
-            float ms = 0.f;
-            if (!(rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) {
-                RT_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-                for (int r = 0; r < 3 && !rc; ++r) rc = launch_rhs_core(ctx, parts, nullptr, ctx->stream);
-                RT_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
-                RT_CUDA(ctx, cudaEventSynchronize(e1));
-                RT_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
-            }
-            if (!rc && ms > best_ms) {  // calibration did not help: back to uniform costs
-                for (int part = 0; part < 3; ++part) ctx->part_scale[part] = scale0[part];
-                rc = split_tables(ctx, best);
-            }
+        float ms = 0.f;
+        if ((rc = split_tables(ctx, best)) || (rc = time_launches(ctx, parts, e0, e1, 3, &ms))) return rc;
+        if (ms > best_ms) {  // calibration did not help: back to uniform costs
+            for (int part = 0; part < 3; ++part) ctx->part_scale[part] = scale0[part];
+            if ((rc = split_tables(ctx, best))) return rc;
         }
     }
     // L2 prefetch distance, then the share of the work split statically (the rest is taken
     // dynamically by CTAs that finish early)
-    auto time3 = [&](float *ms) -> int {
-        int r2;
-        if ((r2 = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) return r2;
-        RT_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-        for (int r = 0; r < 3; ++r)
-            if ((r2 = launch_rhs_core(ctx, parts, nullptr, ctx->stream))) return r2;
-        RT_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
-        RT_CUDA(ctx, cudaEventSynchronize(e1));
-        RT_CUDA(ctx, cudaEventElapsedTime(ms, e0, e1));
-        return RTBTE_OK;
-    };
-    if (!rc) {
-        static const int dists[] = {0, 2, 3, 4, 6, 8};
-        int best_d = ctx->pf_dist;
-        float best_d_ms = 1e30f;
-        for (int d : dists) {
-            ctx->pf_dist = d;
-            float ms = 0.f;
-            if ((rc = time3(&ms))) break;
-            if (ms < best_d_ms) {
-                best_d_ms = ms;
-                best_d = d;
-            }
+    static const int dists[] = {0, 2, 3, 4, 6, 8};
+    int best_d = ctx->pf_dist;
+    float best_d_ms = 1e30f;
+    for (int d : dists) {
+        ctx->pf_dist = d;
+        float ms = 0.f;
+        if ((rc = time_launches(ctx, parts, e0, e1, 3, &ms))) return rc;
+        if (ms < best_d_ms) {
+            best_d_ms = ms;
+            best_d = d;
         }
-        ctx->pf_dist = best_d;
     }
-    if (!rc) {
-        static const double fracs[] = {1.0, 0.9, 0.8, 0.7, 0.6};
-        double best_f = 1.0;
-        float best_f_ms = 1e30f;
-        for (double f : fracs) {
-            ctx->static_frac = f;
-            float ms = 0.f;
-            if ((rc = split_tables(ctx, best)) || (rc = time3(&ms))) break;
-            if (ms < best_f_ms) {
-                best_f_ms = ms;
-                best_f = f;
-            }
+    ctx->pf_dist = best_d;
+    static const double fracs[] = {1.0, 0.9, 0.8, 0.7, 0.6};
+    double best_f = 1.0;
+    float best_f_ms = 1e30f;
+    for (double f : fracs) {
+        ctx->static_frac = f;
+        float ms = 0.f;
+        if ((rc = split_tables(ctx, best)) || (rc = time_launches(ctx, parts, e0, e1, 3, &ms))) return rc;
+        if (ms < best_f_ms) {
+            best_f_ms = ms;
+            best_f = f;
         }
-        ctx->static_frac = best_f;
-        if (!rc) rc = split_tables(ctx, best);
+    }
+    ctx->static_frac = best_f;
+    *chosen = best;
+    return split_tables(ctx, best);
+}
+
+}  // namespace
+
+// Autotuner of the collision launch.  FP32 has two kernel forms (two entry buffers per warp at
+// 16 warps per SM, or one buffer at 24): the work split is tuned for each form from the same
+// starting point, the two tuned launches are timed over 10 launches each (they often differ by
+// ~2%, less than the spread of 3-launch timings) and the faster is kept for this parts mask.
+int autotune(rtbte_ctx *ctx, unsigned parts, int *chosen) {
+    cudaEvent_t e0, e1;
+    RT_CUDA(ctx, cudaEventCreate(&e0));
+    RT_CUDA(ctx, cudaEventCreate(&e1));
+    struct Tuned {
+        int w, pf;
+        double sf, ps[3];
+        float ms;
+    };
+    auto save = [&](int w, float ms) {
+        return Tuned{w, ctx->pf_dist, ctx->static_frac, {ctx->part_scale[0], ctx->part_scale[1], ctx->part_scale[2]}, ms};
+    };
+    auto load = [&](const Tuned &T) {
+        ctx->pf_dist = T.pf;
+        ctx->static_frac = T.sf;
+        for (int p = 0; p < 3; ++p) ctx->part_scale[p] = T.ps[p];
+        return split_tables(ctx, T.w);
+    };
+    const bool two_forms = ctx->staged && ctx->precision != RTBTE_PREC_FP64;
+    const bool deep0 = ctx->deep[parts];
+    const Tuned start = save(ctx->item_overhead, 0.f);
+    Tuned res[2] = {start, start};
+    int rc = RTBTE_OK, nf = two_forms ? 2 : 1;
+    for (int f = 0; f < nf && !rc; ++f) {
+        if (two_forms) ctx->deep[parts] = f == 1;
+        int w = start.w;
+        float ms = 0.f;
+        if ((rc = load(start)) || (rc = tune_split(ctx, parts, e0, e1, &w))) break;
+        if (two_forms && (rc = time_launches(ctx, parts, e0, e1, 10, &ms))) break;
+        res[f] = save(w, ms);
+    }
+    int pick = 0;
+    if (!rc && two_forms) {
+        pick = res[1].ms < res[0].ms ? 1 : 0;
+        ctx->deep[parts] = pick == 1;
+        ctx->deep_tuned |= 1u << parts;
+    }
+    if (rc) {  // back to the starting launch parameters
+        ctx->deep[parts] = deep0;
+        load(start);
+    } else {
+        rc = load(res[pick]);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    if (chosen) *chosen = best;
+    if (chosen) *chosen = res[pick].w;
     return RTBTE_OK;
 }
 

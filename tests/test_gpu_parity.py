@@ -176,6 +176,28 @@ def test_autotune_keeps_results_bitwise(rt):
     ctx.close()
 
 
+@pytest.mark.parametrize("which", ["wide", "sub-warp"])
+def test_fp32_launch_forms_agree_bitwise(rt, which):
+    """The two FP32 launch forms (two entry buffers per warp at 16 warps per SM; one buffer at
+    24) compute every item partial with the same arithmetic.  By default a launch with e-ph work
+    takes the 24-warp form and a ph-e-only launch the 16-warp form, so the phonon rows of
+    parts = e-ph + ph-e (only ph-e items reach them) equal those of parts = ph-e bit for bit."""
+    ms = [ri.graphene_small(36)] if which == "wide" else [ri.graphene_small(24), ri.graphene(n=30, window=0.6, seed=77)]
+    ctx = rt.Context(ms)
+    for i in range(len(ms)):
+        ctx.upload_channels(i)
+    y = torch.tensor(np.concatenate([sym_state(m, 21 + i) for i, m in enumerate(ms)]), device="cuda")
+    both = ctx.rhs(y, parts=EPH | PHE).cpu().numpy()
+    phe = ctx.rhs(y, parts=PHE).cpu().numpy()
+    off = 0
+    for m in ms:
+        ph = slice(off + m.n_c, off + m.n_c + m.n_ph)
+        assert np.array_equal(both[ph], phe[ph])
+        assert np.any(phe[ph] != 0.0)
+        off += m.n_c + m.n_ph
+    ctx.close()
+
+
 def test_batched_instances_equal_single_contexts(rt):
     ms = [ri.graphene_small(24), ri.graphene_small(36, seed=5), ri.graphene(n=30, window=0.6, seed=77)]
     ctx = rt.Context(ms)

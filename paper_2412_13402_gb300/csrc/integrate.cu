@@ -162,8 +162,15 @@ __global__ void __launch_bounds__(kRedThreads) stage_kernel(RowParams Q, StageAr
     }
     const InstDev I = Q.inst[0];
     if (a.respect_done && a.ctl[0].done) return;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.n; c += (long long)gridDim.x * blockDim.x)
-        stage_row<R>(Q, a, 0, I, c);
+    // 32-row chunks dealt round-robin over the blocks (warp w of block b takes chunk w * grid + b
+    // first), so that the electron rows, which sum many more item partials than phonon rows and
+    // come first in the state, spread over every SM instead of filling the first blocks
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long nch = (a.n + 31) >> 5;
+    for (long long ch = (long long)w * gridDim.x + blockIdx.x; ch < nch; ch += (long long)gridDim.x * nw) {
+        const long long c = (ch << 5) + lane;
+        if (c < a.n) stage_row<R>(Q, a, 0, I, c);
+    }
 }
 
 // Fixed-order sum of v[b .. b+n) by one block.
@@ -437,7 +444,9 @@ int n_inst(rtbte_ctx *ctx) { return (int)ctx->inst.size(); }
 
 template <class R>
 int launch_stage(rtbte_ctx *ctx, const StageArgs &a, cudaStream_t s) {
-    const int grid = a.rblk ? std::min(a.nrblk, 8 * ctx->num_sms) : row_grid(ctx);
+    const long long want = a.rblk ? a.nrblk : (ctx->n_y + kRedThreads - 1) / kRedThreads;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(want, ctx->stage_resident > 0 ? ctx->stage_resident
+                                                                                               : 2 * ctx->num_sms));
     stage_kernel<R><<<grid, kRedThreads, 0, s>>>(row_params(ctx), a);
     RT_CUDA(ctx, cudaGetLastError());
     ctx->launches++;
@@ -782,6 +791,20 @@ void gather_stats(rtbte_ctx *ctx, rtbte_stats *st, bool add_steps) {
 }
 
 }  // namespace
+
+// The stage kernel's grid is the number of its blocks resident on the whole GPU: a larger
+// grid leaves a second partial wave of blocks (at 80 registers, 3 blocks of 256 threads fit an
+// SM, so 512 blocks ran as 456 + 56 and the SMs holding the second wave took 1.7x the mean).
+int init_stage_grid(rtbte_ctx *ctx) {
+    int nb = 0;
+    if (ctx->precision == RTBTE_PREC_FP64)
+        RT_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage_kernel<double>, kRedThreads, 0));
+    else
+        RT_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage_kernel<float>, kRedThreads, 0));
+    ctx->stage_resident = std::max(nb, 1) * ctx->num_sms;
+    return RTBTE_OK;
+}
+
 
 int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *o, rtbte_stats *st) {
     rtbte_stats local;

@@ -220,6 +220,7 @@ struct rtbte_ctx {
     int n_items = 0, n_groups = 0;
     int part_items[3] = {0, 0, 0};
     int part_first[3] = {0, 0, 0};
+    int stage_resident = 0;    // stage kernel: blocks resident on the whole GPU at once (its grid)
     int grid = 0, per_sm = 1;  // collision kernel: CTAs per SM (1, 2 or 4; threads = form's threads per SM / per_sm)
     bool deep[8] = {};         // FP32 launches of parts mask m use the single-buffer 768-thread form
     unsigned deep_tuned = 0;   // masks whose form the autotuner chose (kept across plans)
@@ -275,6 +276,7 @@ int autotune(rtbte_ctx *ctx, unsigned parts, int *chosen);
 // integrate.cu
 int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *opt, rtbte_stats *st);
 void destroy_graphs(rtbte_ctx *ctx);
+int init_stage_grid(rtbte_ctx *ctx);  // resident blocks of the stage kernel (before any capture)
 // api.cu
 int fail(rtbte_ctx *ctx, int code, const std::string &msg);
 int launch_pp_rates(rtbte_ctx *ctx, int inst, double *rates, cudaStream_t s);

@@ -980,6 +980,7 @@ int make_plan(rtbte_ctx *ctx) {
     ctx->partials.bytes = pb;
     RT_CUDA(ctx, cudaMemsetAsync(ctx->partials.p, 0, pb, ctx->stream));
     RT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if ((rc = init_stage_grid(ctx))) return rc;
     ctx->plan_valid = true;
     return RTBTE_OK;
 }

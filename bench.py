@@ -48,7 +48,7 @@ WORKLOAD = "graphene-like 2D: 2 Dirac bands on 180x180 k-grid (1 eV window, 1272
 
 
 STUDIES = ("accuracy", "ensemble", "ensemble_ab", "surrogate", "silicon", "silicon_printed", "graphene_long",
-           "silicon_long")
+           "silicon_long", "phph_rates")
 
 
 def parse():
@@ -63,7 +63,8 @@ def parse():
                          "sweep; ensemble = the 64-instance batched ensemble; ensemble_ab = batched against one "
                          "context per instance at population error <= 1e-6; surrogate = the learned slow stage; "
                          "silicon = config 3 at reduced grids; silicon_printed = config 3 at the printed grids; "
-                         "graphene_long / silicon_long = the configs' full integration lengths")
+                         "graphene_long / silicon_long = the configs' full integration lengths; phph_rates = grid "
+                         "convergence of the linearised mode-resolved 300 K ph-ph rates")
     ap.add_argument("--cpu-table", action="store_true",
                     help="print only the FP64 oracle's CPU-baseline table on this host (no GPU work)")
     ap.add_argument("--direct-launches", action="store_true",
@@ -911,6 +912,43 @@ def silicon_long_study(rt, ri, dev, t_end=20.0, window=1.0, fp64_t_end=None):
     return out
 
 
+def phph_rates_study(rt, ri, dev, sides=(90, 120, 150, 180, 240)):
+    """Grid convergence of the linearised mode-resolved ph-ph rates at 300 K (the tool the paper
+    uses to choose its phonon grids, Methods A, silicon): for the graphene-like model at k/q-grid
+    side n (ph-ph on the stride-3 sub-lattice of side n/3, the benchmark's sigma_pp = 2 meV), the
+    rates -dI^{ph-ph}_a/dN_a at Bose-Einstein populations, averaged per branch over the sub-lattice
+    points that scatter, with each branch's change against the next finer grid."""
+    import numpy as np
+    import torch
+
+    names = ("LA", "TA", "ZA", "ZO", "TO", "LO")
+    grids = []
+    for n in sides:
+        m = ri.graphene(n=n)
+        c = rt.Context(m, precision="fp64", device=dev.index or 0)
+        c.upload_channels()
+        y = torch.tensor(m.y0(), device=dev)  # phonons: Bose-Einstein at 300 K
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = c.phph_rates(y)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        sz = c.sizes(0)
+        c.close()
+        rp = r.cpu().numpy()[m.n_c:].reshape(m.nmodes, -1)
+        per = {}
+        for nu in range(m.nmodes):
+            v = rp[nu][rp[nu] > 0.0]
+            per[names[nu]] = {"mean_per_ps": float(v.mean()) if v.size else 0.0,
+                              "median_per_ps": float(np.median(v)) if v.size else 0.0, "points": int(v.size)}
+        grids.append({"side": n, "phph_side": n // 3, "pp_entries": sz["pp_entries"], "rates_call_s": dt,
+                      "branches": per})
+    for a, b in zip(grids[:-1], grids[1:]):
+        a["change_to_next_grid"] = {k: (b["branches"][k]["mean_per_ps"] / a["branches"][k]["mean_per_ps"] - 1.0)
+                                    if a["branches"][k]["mean_per_ps"] > 0 else None for k in names}
+    return {"study": "phph_rates", "model": "graphene-like, sigma_pp 2 meV, T 300 K, FP64 sums", "grids": grids}
+
+
 def surrogate_study(rt, ri, dev, t_end=0.5, n_traj=40, states_per=500, dt_collect=0.004):
     """Config 5, the learned slow stage, at the accuracy the target asks for (population error
     <= 1e-6 over 0.5 ps against the FP64 reference of the error protocol).
@@ -1257,7 +1295,8 @@ def main():
               "silicon": lambda: silicon_study(rt, ri, dev),
               "silicon_printed": lambda: silicon_printed_study(rt, ri, dev),
               "graphene_long": lambda: graphene_long_study(rt, ri, dev),
-              "silicon_long": lambda: silicon_long_study(rt, ri, dev)}[args.study]
+              "silicon_long": lambda: silicon_long_study(rt, ri, dev),
+              "phph_rates": lambda: phph_rates_study(rt, ri, dev)}[args.study]
         print(json.dumps({"study": args.study, **fn()}), flush=True)
         return 0
     return run_ours(args)

@@ -96,8 +96,7 @@ struct StageArgs {
     unsigned parts;
     int stage;         // -1: populations <- y; 0..S-1: combine stage `stage`
     int respect_done;  // inside an attempt sequence: skip instances whose integration is done
-    const int4 *rblk;  // several instances: row blocks {instance, first row, end row, 0} (else null)
-    int nrblk;
+    int batched;       // several instances: rows visited by row blocks of active instances only
 };
 
 __device__ __forceinline__ double atol_of(const CtlParams &cp, const InstDev &I, long long local) {
@@ -146,17 +145,65 @@ __device__ __forceinline__ void stage_row(const RowParams &Q, const StageArgs &a
     }
 }
 
-// Stage combination over the rows.  Several instances: the grid walks a table of row blocks of
-// one instance each, so a finished instance's blocks are skipped whole and no row looks up its
-// instance; one instance: a grid-stride loop over its rows.
+// Exclusive prefix of v over the threads of the block (thread order); *total = the block's sum.
+// Called by every thread of the block, once per kernel.
+__device__ int block_excl_scan(int v, int *total) {
+    __shared__ int ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) ws[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < nw ? ws[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane < nw) ws[lane] = w;
+    }
+    __syncthreads();
+    *total = ws[nw - 1];
+    return incl - v + (wid > 0 ? ws[wid - 1] : 0);
+}
+
+// Stage combination over the rows.  Several instances: every block first lists the row blocks
+// (kRedThreads rows of one instance, one row per thread) of the instances still integrating --
+// a prefix over instances in shared memory -- and the grid walks only those, so a launch late in
+// a batched integration, with a few slow instances left, costs their rows and nothing else.  One
+// instance: a grid-stride loop over its rows.
 template <class R>
 __global__ void __launch_bounds__(kRedThreads) stage_kernel(RowParams Q, StageArgs a) {
-    if (a.rblk) {
-        for (int b = blockIdx.x; b < a.nrblk; b += gridDim.x) {
-            const int4 t = a.rblk[b];
-            if (a.respect_done && a.ctl[t.x].done) continue;
-            const InstDev I = Q.inst[t.x];
-            for (long long c = t.y + threadIdx.x; c < t.z; c += blockDim.x) stage_row<R>(Q, a, t.x, I, c);
+    if (a.batched) {
+        __shared__ int s_pre[kMaxBatch + 1];  // s_pre[i]: first active row block of instance i
+        const int NI = Q.n_inst;              // <= kMaxBatch (checked on the host)
+        const int C = (NI + blockDim.x - 1) / blockDim.x;
+        const int i0 = threadIdx.x * C;
+        int run = 0;
+        for (int i = i0; i < i0 + C && i < NI; ++i) {
+            if (!(a.respect_done && a.ctl[i].done)) {
+                const long long rows = (long long)Q.inst[i].n_c + Q.inst[i].n_ph;
+                run += (int)((rows + kRedThreads - 1) / kRedThreads);
+            }
+            s_pre[i + 1] = run;
+        }
+        int total;
+        const int before = block_excl_scan(run, &total);
+        for (int i = i0; i < i0 + C && i < NI; ++i) s_pre[i + 1] += before;
+        if (threadIdx.x == 0) s_pre[0] = 0;
+        __syncthreads();
+        for (int b = blockIdx.x; b < total; b += gridDim.x) {
+            int lo = 0, hi = NI - 1;  // the last instance with s_pre[i] <= b (an active one)
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_pre[mid] <= b) lo = mid; else hi = mid - 1;
+            }
+            const InstDev I = Q.inst[lo];
+            const long long r = (long long)(b - s_pre[lo]) * kRedThreads + threadIdx.x;
+            if (r < (long long)I.n_c + I.n_ph) stage_row<R>(Q, a, lo, I, I.y_off + r);
         }
         return;
     }
@@ -444,7 +491,7 @@ int n_inst(rtbte_ctx *ctx) { return (int)ctx->inst.size(); }
 
 template <class R>
 int launch_stage(rtbte_ctx *ctx, const StageArgs &a, cudaStream_t s) {
-    const long long want = a.rblk ? a.nrblk : (ctx->n_y + kRedThreads - 1) / kRedThreads;
+    const long long want = a.batched ? ctx->n_rblk : (ctx->n_y + kRedThreads - 1) / kRedThreads;
     const int grid = (int)std::max<long long>(1, std::min<long long>(want, ctx->stage_resident > 0 ? ctx->stage_resident
                                                                                                : 2 * ctx->num_sms));
     stage_kernel<R><<<grid, kRedThreads, 0, s>>>(row_params(ctx), a);
@@ -471,10 +518,7 @@ StageArgs stage_args(rtbte_ctx *ctx, const Tableau &T, const CtlParams &cp, unsi
     a.wsq = ctx->wrms_part.as<double>();
     a.n = ctx->n_y;
     a.parts = parts;
-    if (n_inst(ctx) > 1) {
-        a.rblk = ctx->rblk.as<int4>();
-        a.nrblk = ctx->n_rblk;
-    }
+    a.batched = n_inst(ctx) > 1 ? 1 : 0;
     return a;
 }
 

@@ -36,6 +36,7 @@ constexpr int kMaxModes = 16;
 constexpr int kMaxStages = 5;
 constexpr int kWrmsBlocks = 512;
 constexpr int kWrmsChunks = 128;  // per-instance blocks of the WRMS reduction before the controller
+constexpr int kMaxBatch = 1024;  // instances per context (shared-memory tables of the batched kernels)
 constexpr int kLoopCap = 64;     // attempts per launch of an attempt-loop graph (default)
 
 enum { PART_EPH = 0, PART_PHE = 1, PART_PP = 2 };
@@ -215,8 +216,7 @@ struct rtbte_ctx {
     // execution plan of the RHS
     bool plan_valid = false;
     rtbte::DevBuf items, groups, partials, eoff, poff, ppoff, cta_tab, gwt, dyn_tab;
-    rtbte::DevBuf rblk;  // several instances: row blocks {instance, first row, end row, 0} of the stage kernels
-    int n_rblk = 0;
+    int n_rblk = 0;  // several instances: row blocks of the stage kernels (256 rows of one instance each)
     int n_items = 0, n_groups = 0;
     int part_items[3] = {0, 0, 0};
     int part_first[3] = {0, 0, 0};

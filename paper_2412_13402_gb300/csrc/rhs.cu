@@ -511,12 +511,22 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(KParams P) {
 // A CTA then visits only the active groups act[out_act[c]], ... overlapping its item range,
 // so finished instances cost it nothing.
 __global__ void split_kernel(const Group *groups, int n_groups, const long long *gw, const Ctl *ctl, unsigned mask,
-                             int grid, int *out, int *out_act, int *act) {
+                             int grid, int *out, int *out_act, int *act, int *memo, int n_inst) {
     __shared__ long long A[1025];   // inclusive prefix of active weight over groups (A[0] = 0)
     __shared__ int Cn[1025];        // active groups before group g
     __shared__ long long wsum[32];
     __shared__ int csum[32];
+    __shared__ int s_same;
     const int T = blockDim.x;  // 256 threads, n_groups <= 1024 (checked on the host)
+    // the tables of the last split still hold when the same instances are active for the same
+    // parts (memo: the done flags and mask it was made for, and a flag the host clears whenever
+    // the item weights change)
+    if (threadIdx.x == 0) s_same = memo[n_inst + 1] == 1 && memo[n_inst] == (int)mask;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_inst; i += T)
+        if (memo[i] != ctl[i].done) s_same = 0;
+    __syncthreads();
+    if (s_same) return;
     const int C = (n_groups + T - 1) / T;
     const int g0 = threadIdx.x * C;
     long long run = 0;
@@ -602,6 +612,11 @@ __global__ void split_kernel(const Group *groups, int n_groups, const long long 
         const long long ni = G.item_end - G.item_begin;
         out[c] = G.item_begin + (int)((t - A[lo]) * ni / (wg > 0 ? wg : 1));
         out_act[c] = Cn[lo];
+    }
+    for (int i = threadIdx.x; i < n_inst; i += T) memo[i] = ctl[i].done;
+    if (threadIdx.x == 0) {
+        memo[n_inst] = (int)mask;
+        memo[n_inst + 1] = 1;
     }
 }
 
@@ -727,6 +742,10 @@ int split_tables(rtbte_ctx *ctx, int overhead) {
     }
     int rc;
     if ((rc = upload_vec(ctx, ctx->gwt, gwt))) return rc;
+    // the device re-split's memo no longer matches the weights: clear its valid flag
+    const size_t valid_at = 2 * (size_t)ctx->grid + 1 + ctx->n_groups + 1 + ctx->inst.size() + 1;
+    if (ctx->dyn_tab.p && (valid_at + 1) * sizeof(int) <= ctx->dyn_tab.bytes)
+        RT_CUDA(ctx, cudaMemsetAsync(ctx->dyn_tab.as<int>() + valid_at, 0, sizeof(int), ctx->stream));
     if (tail.empty()) tail.push_back(make_int4(0, 0, 0, 0));
     if ((rc = upload_vec(ctx, ctx->tail_tab, tail))) return rc;
     return upload_vec(ctx, ctx->cta_tab, tab);
@@ -958,22 +977,21 @@ int make_plan(rtbte_ctx *ctx) {
     if ((rc = upload_vec(ctx, ctx->ppoff, ppoff))) return rc;
     if ((rc = upload_vec(ctx, ctx->instdev, idev))) return rc;
     if ((rc = upload_vec(ctx, ctx->compact, compact))) return rc;
-    std::vector<int4> rblk;  // row blocks of 1024 rows within one instance (batched stage kernels)
-    if (ctx->inst.size() > 1)
-        for (size_t i = 0; i < ctx->inst.size(); ++i) {
-            const InstHost &I = ctx->inst[i];
-            const long long e = I.y_off + I.d.n_c + I.n_ph;
-            for (long long r = I.y_off; r < e; r += 1024)
-                rblk.push_back(make_int4((int)i, (int)r, (int)std::min(e, r + 1024), 0));
-        }
     if (ctx->n_y >= (long long)INT32_MAX) return fail(ctx, RTBTE_E_UNSUPPORTED, "state vector too long");
-    ctx->n_rblk = (int)rblk.size();
-    if ((rc = upload_vec(ctx, ctx->rblk, rblk))) return rc;
+    if (ctx->inst.size() > (size_t)kMaxBatch) return fail(ctx, RTBTE_E_UNSUPPORTED, "more than 1024 instances");
+    long long nrb = 0;  // row blocks of 256 rows of one instance (batched stage kernels)
+    if (ctx->inst.size() > 1)
+        for (const InstHost &I : ctx->inst) nrb += (I.d.n_c + I.n_ph + 255) / 256;
+    ctx->n_rblk = (int)nrb;
+    ctx->dyn_tab.release();  // reallocated below for this plan's sizes
     if ((rc = split_tables(ctx, ctx->item_overhead))) return rc;
     if (ctx->n_groups > 1024) return fail(ctx, RTBTE_E_UNSUPPORTED, "more than 1024 staging groups");
+    // device re-split tables: [grid+1] item bounds, [grid] act indices, [n_groups+1] active groups,
+    // then the memo of the last split: [n_inst] done flags it saw, its parts mask, a valid flag
     ctx->dyn_tab.release();
-    ctx->dyn_tab.bytes = sizeof(int) * (2 * ctx->grid + 1 + ctx->n_groups + 1);
+    ctx->dyn_tab.bytes = sizeof(int) * (2 * ctx->grid + 1 + ctx->n_groups + 1 + ctx->inst.size() + 2);
     RT_CUDA(ctx, cudaMalloc(&ctx->dyn_tab.p, ctx->dyn_tab.bytes));
+    RT_CUDA(ctx, cudaMemsetAsync(ctx->dyn_tab.p, 0, ctx->dyn_tab.bytes, ctx->stream));
     ctx->partials.release();
     size_t pb = std::max<size_t>(2 * R * (size_t)std::max(ctx->n_items, 1), 16);
     RT_CUDA(ctx, cudaMalloc(&ctx->partials.p, pb));
@@ -1008,9 +1026,10 @@ static int launch_core_t(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStr
     P.mask = parts;
     P.pf_dist = ctx->pf_dist;
     if (ctl && ctx->inst.size() > 1) {  // batched integration: balance over the active instances
-        int *dt = ctx->dyn_tab.as<int>();  // [grid+1] item bounds, [grid] act indices, [n_groups+1] act
+        int *dt = ctx->dyn_tab.as<int>();  // [grid+1] item bounds, [grid] act indices, [n_groups+1] act, memo
         split_kernel<<<1, 256, 0, s>>>(ctx->groups.as<Group>(), ctx->n_groups, ctx->gwt.as<long long>(), ctl, parts,
-                                       ctx->grid, dt, dt + ctx->grid + 1, dt + 2 * ctx->grid + 1);
+                                       ctx->grid, dt, dt + ctx->grid + 1, dt + 2 * ctx->grid + 1,
+                                       dt + 2 * ctx->grid + 1 + ctx->n_groups + 1, (int)ctx->inst.size());
         RT_CUDA(ctx, cudaGetLastError());
         ctx->launches++;
         P.cta_items = dt;

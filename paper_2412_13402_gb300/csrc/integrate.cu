@@ -220,19 +220,19 @@ __global__ void __launch_bounds__(kRedThreads) stage_kernel(RowParams Q, StageAr
     }
 }
 
-// Fixed-order sum of v[b .. b+n) by one block.
+// Fixed-order sum of v[b .. b+n) by one block: strided per-thread sums, a butterfly within each
+// warp (both partners of a pair add the same two values, so every lane holds the same bits), then
+// the warp sums in warp order.  Every thread returns the sum.
 __device__ double block_sum(const double *v, long long b, long long n) {
-    __shared__ double red[kRedThreads];
+    __shared__ double ws[kRedThreads / 32];
     double acc = 0.0;
     for (long long r = threadIdx.x; r < n; r += blockDim.x) acc += v[b + r];
-    red[threadIdx.x] = acc;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
     __syncthreads();
-    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    const double r = red[0];
-    __syncthreads();
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += ws[w];
+    __syncthreads();  // ws is free for the next call
     return r;
 }
 
@@ -274,10 +274,18 @@ __global__ void controller_kernel(RowParams Q, Ctl *ctl, CtlParams cp, const dou
     const InstDev I = Q.inst[blockIdx.x];
     const long long ni = (long long)I.n_c + I.n_ph;
     const double sum = block_sum(part, (long long)blockIdx.x * kWrmsChunks, kWrmsChunks);
+    if (threadIdx.x >= 32) return;
+    const double eps = sqrt(sum / (double)ni);
+    // logarithms of the three PID factors, one per lane, ahead of the scalar logic of thread 0:
+    // FP64 transcendental functions are slow in a single thread on this GPU, and the three are
+    // independent (lane 0: the floored error norm, lanes 1-2: the two previous ones)
+    double lg = 0.0;
+    if (threadIdx.x < 3) lg = log(threadIdx.x == 0 ? fmax(eps, 1e-10) : threadIdx.x == 1 ? c->eps1 : c->eps2);
+    const double lg1 = __shfl_sync(0xffffffffu, lg, 1), lg2 = __shfl_sync(0xffffffffu, lg, 2);
     if (threadIdx.x != 0) return;
+    const double lg0 = lg;
     const unsigned long long nr = range[blockIdx.x];
     range[blockIdx.x] = 0;
-    const double eps = sqrt(sum / (double)ni);
     c->attempts++;
     if (!isfinite(eps)) {
         c->status = RTBTE_E_NONFINITE;
@@ -302,8 +310,9 @@ __global__ void controller_kernel(RowParams Q, Ctl *ctl, CtlParams cp, const dou
         c->steps++;
         c->range_viol += (long long)nr;
         const double e = eps > 1e-10 ? eps : 1e-10;
-        double eta = cp.pid_sign_mode == 0 ? pow(e, -cp.a1 / p) * pow(c->eps1, cp.a2 / p) * pow(c->eps2, -cp.a3 / p)
-                                           : pow(e, -cp.a1 / p) * pow(c->eps1, -cp.a2 / p) * pow(c->eps2, -cp.a3 / p);
+        // e^(-a1/p) eps1^(+-a2/p) eps2^(-a3/p) as one exponential of the lanes' logarithms
+        const double x2 = cp.pid_sign_mode == 0 ? cp.a2 / p : -cp.a2 / p;
+        double eta = exp((-cp.a1 / p) * lg0 + x2 * lg1 + (-cp.a3 / p) * lg2);
         eta *= cp.safety;
         double cap = c->first ? cp.growth_first : cp.growth;
         if (c->nef > 0 && cap > 1.0) cap = 1.0;
@@ -338,7 +347,7 @@ __global__ void controller_kernel(RowParams Q, Ctl *ctl, CtlParams cp, const dou
             c->done = 1;
             return;
         }
-        double eta = cp.safety * pow(eps, -1.0 / p);
+        double eta = cp.safety * exp((-1.0 / p) * lg0);  // eps^(-1/p); eps > 1 here, so lg0 = log(eps)
         if (eta < cp.etamin) eta = cp.etamin;
         if (eta > 1.0) eta = 1.0;
         if (c->nef >= cp.small_nef && eta > cp.etamxf) eta = cp.etamxf;

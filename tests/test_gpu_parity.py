@@ -247,6 +247,36 @@ def test_batched_integration_has_independent_controllers(rt, method):
     ctx.close()
 
 
+def test_batched_windows_equal_single_contexts(rt):
+    """Three consecutive windows of a batched integration (controllers resumed, instances
+    finishing each window at different attempts, so the device re-split of the active groups is
+    recomputed, reused and recomputed again) equal the same windows of each instance alone."""
+    ms = [ri.graphene_small(24), ri.graphene_small(36, seed=5), ri.graphene(n=30, window=0.6, seed=77)]
+    kw = dict(method="zon43", rtol=1e-5, atol_c=1e-9, atol_ph=1e-12)
+    ctx = rt.Context(ms)
+    for i in range(len(ms)):
+        ctx.upload_channels(i)
+    y = torch.tensor(np.concatenate([m.y0() for m in ms]), device="cuda")
+    singles = []
+    for m in ms:
+        c1 = rt.Context(m)
+        c1.upload_channels()
+        singles.append((c1, torch.tensor(m.y0(), device="cuda")))
+    for w, (t0, t1) in enumerate(((0.0, 0.01), (0.01, 0.02), (0.02, 0.03))):
+        st = ctx.advance_to(t1, y, t0=t0, resume=1 if w else 0, **kw)
+        assert st["status"] == 0
+        for c1, y1 in singles:
+            assert c1.advance_to(t1, y1, t0=t0, resume=1 if w else 0, **kw)["status"] == 0
+        got = y.cpu().numpy()
+        off = 0
+        for m, (c1, y1) in zip(ms, singles):
+            assert np.array_equal(got[off:off + m.n_y], y1.cpu().numpy()), (w, m.name)
+            off += m.n_y
+    for c1, _ in singles:
+        c1.close()
+    ctx.close()
+
+
 def test_full_graphene_workload_sampled(rt, oracle_lib):
     """The 180 x 180 graphene-like workload in the launch configuration the benchmark uses:
     sampled channel segments bit-exact and sampled RHS rows within 1e-5 of the literal sums."""

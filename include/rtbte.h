@@ -103,7 +103,9 @@ typedef struct rtbte_instance_desc {
 } rtbte_instance_desc;
 
 typedef struct rtbte_desc {
-    int32_t n_instances;  /* independent simulations sharing one state vector        */
+    int32_t n_instances;  /* independent simulations sharing one state vector (1..1024;
+                             the first collision evaluation refuses more than 1024
+                             instances or staging groups with UNSUPPORTED)             */
     int32_t precision;    /* RTBTE_PREC_*                                           */
     const rtbte_instance_desc *inst; /* host [n_instances]                           */
     double hbar;          /* eV*ps                                                   */

@@ -949,7 +949,7 @@ def phph_rates_study(rt, ri, dev, sides=(90, 120, 150, 180, 240)):
     return {"study": "phph_rates", "model": "graphene-like, sigma_pp 2 meV, T 300 K, FP64 sums", "grids": grids}
 
 
-def surrogate_study(rt, ri, dev, t_end=0.5, n_traj=40, states_per=500, dt_collect=0.004):
+def surrogate_study(rt, ri, dev, t_end=0.5, n_traj=40, states_per=500, dt_collect=0.004, long_ps=100.0):
     """Config 5, the learned slow stage, at the accuracy the target asks for (population error
     <= 1e-6 over 0.5 ps against the FP64 reference of the error protocol).
     1. Pairs (N, exact I^{ph-ph}) from the method's own trajectories: n_traj initial conditions of
@@ -965,7 +965,10 @@ def surrogate_study(rt, ri, dev, t_end=0.5, n_traj=40, states_per=500, dt_collec
     5. A/B over t_end at the MRI settings of the error protocol (h_s 20 fs and 100 fs, fast rtol
        1e-4): plain MRI against surrogate MRI with the exact judge every 10 or every slow step at
        that tolerance (fallbacks counted), and with the tolerance unbounded (never detached);
-       plus the slow part's share of plain MRI's kernel time, the most any surrogate can save."""
+       plus the slow part's share of plain MRI's kernel time, the most any surrogate can save.
+    6. The config's integration length: the same MRI (h_s 20 fs, judge every 10 slow steps) to
+       long_ps, plain against surrogate (judge tolerance from the target, and never detached),
+       the surrogate runs' end states compared with plain MRI's."""
     import numpy as np
     import torch
 
@@ -1078,13 +1081,45 @@ def surrogate_study(rt, ri, dev, t_end=0.5, n_traj=40, states_per=500, dt_collec
     plain = {r["h_s_fs"]: r for r in ab if r["variant"] == "plain MRI"}
     slow_share = {f"h_s_{int(k)}fs": (v["slow_exact"] * exact_ms) / (v["slow_exact"] * exact_ms + v["rhs_fast"] * fast_ms)
                   for k, v in plain.items()}
+
+    # the config's integration length: MRI (h_s 20 fs, exact judge every 10 slow steps) to long_ps,
+    # the surrogate runs compared with plain MRI at the same settings (the error the surrogate adds)
+    def run_long(tag, period=None, tol=None, h_s=0.020):
+        if period is not None:
+            sur.attach(judge_period=period, judge_tol=tol)
+        y = y0.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        st = ctx.advance_to(long_ps, y, t0=0.0, method="mri", h_s=h_s, rtol=1e-4, atol_c=1e-9, atol_ph=1e-12)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        if period is not None:
+            sur.detach()
+        sec = e0.elapsed_time(e1) / 1000.0
+        return y.cpu().numpy(), {"variant": tag, "judge_period": period, "judge_tol": tol, "status": st["status"],
+                                 "t_ps": st["t"], "seconds": sec, "sim_ps_per_s": st["t"] / sec,
+                                 "slow_exact": st["slow_exact"], "slow_surrogate": st["slow_surrogate"],
+                                 "fallbacks": st["surrogate_fallbacks"], "judge_err_max": st["judge_err_max"]}
+
+    long_runs = []
+    if long_ps > 0:
+        yp, rp = run_long("plain MRI")
+        long_runs.append(rp)
+        for tag, period, tol in (("surrogate MRI, judge tolerance from the 1e-6 target", 10, 1e-6 / (10 * 0.020 * ratio)),
+                                 ("surrogate MRI, never detached", 10, 1e30)):
+            yv, rv = run_long(tag, period, tol)
+            if rv["status"] == 0:
+                rv["vs_plain_carriers"] = float(np.linalg.norm(yv[:nc] - yp[:nc]) / np.linalg.norm(yp[:nc]))
+                rv["vs_plain_phonons"] = float(np.linalg.norm(yv[nc:] - yp[nc:]) / np.linalg.norm(yp[nc:]))
+            long_runs.append(rv)
     sur.close()
     ctx.close()
     return {"pairs": n_traj * states_per, "trajectories": n_traj, "collect_s": collect_s, "train_steps": [4000, 4000],
             "batch": 8, "train_s": train_s, "loss_abs": l_abs, "loss_diff": l_diff, "exact_slow_ms": exact_ms,
             "fast_rhs_ms": fast_ms, "inference_ms": infer_ms, "slow_value_error": slow_err,
             "I_pp_over_N_per_ps": ratio, "slow_share_of_plain_mri_kernel_time": slow_share, "t_end_ps": t_end,
-            "ab": ab}
+            "ab": ab, "long_ps": long_ps, "long": long_runs}
 
 
 def headline(*, value, n_gpus, steps, warmup, ms_per_step, config, sim_ps_per_s, sim_ps_at_1e6, roofline, e2e,

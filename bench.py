@@ -581,6 +581,9 @@ def accuracy_sweep(rt, ri, dev, t_end=0.5, quick=False):
         c.upload_channels()
         c.rhs(y0, torch.empty_like(y0))
         c.autotune(rt.RTBTE_ALL)
+        if prec == "fp32":  # MRI's fast and slow launches keep their own parameters
+            c.autotune(rt.RTBTE_FAST)
+            c.autotune(rt.RTBTE_SLOW)
         ctxs[prec] = c
     ref, st_ref, t_ref = run(ctxs["fp64"], method="zon43", rtol=1e-9, atol_c=1e-15, atol_ph=1e-15)
     assert st_ref["status"] == 0, st_ref
@@ -1160,6 +1163,8 @@ def run_ours(args):
     y = torch.tensor(m.y0(), device=dev)
     ctx.rhs(y, torch.empty_like(y))
     split_weight = ctx.autotune(rt.RTBTE_ALL)  # setup: work-split weight of the persistent grid
+    ctx.autotune(rt.RTBTE_FAST)  # the MRI leg's fast and slow launches (their own parameters)
+    ctx.autotune(rt.RTBTE_SLOW)
 
     def barrier():
         torch.cuda.synchronize()

@@ -330,13 +330,15 @@ int rtbte_set_stream(rtbte_ctx *ctx, void *stream);
  * In FP32 the kernel also has two launch forms, two register buffers of entries per warp at 16
  * warps per SM or one buffer at 24 warps per SM, chosen per parts mask.
  * This call times the kernel for `parts` over the forms and candidates of w, c_part, d and s and
- * keeps the fastest (w in *chosen when not NULL).  Synchronises the stream; results of later calls do
- * not depend on the choice (rows add item partials in a fixed order).
+ * keeps the fastest for that parts mask (w in *chosen when not NULL); masks never tuned
+ * themselves take its w, c_part, d and s.  Each parts mask keeps its own parameters, so tuning
+ * the fast and slow masks of MRI does not change the full-RHS launch.  Synchronises the stream;
+ * results of later calls do not depend on the choice (rows add item partials in a fixed order).
  * Errors: INVALID_ARG, STATE, CUDA. */
 int rtbte_autotune(rtbte_ctx *ctx, unsigned parts, int *chosen);
 
-/* The launch parameters in use: w, d and s as described for rtbte_autotune (any pointer may be
- * NULL).  Errors: INVALID_ARG. */
+/* The launch parameters of the full-RHS mask (RTBTE_ALL): w, d and s as described for
+ * rtbte_autotune (any pointer may be NULL).  Errors: INVALID_ARG. */
 int rtbte_get_tuning(const rtbte_ctx *ctx, int32_t *item_weight, int32_t *prefetch_items, double *static_share);
 
 /* How rtbte_advance_to runs attempts: 1 (default) as one launch of the device-loop CUDA graph

@@ -674,9 +674,10 @@ int rtbte_autotune(rtbte_ctx *ctx, unsigned parts, int *chosen) {
 
 int rtbte_get_tuning(const rtbte_ctx *ctx, int32_t *item_weight, int32_t *prefetch_items, double *static_share) {
     if (!ctx) return RTBTE_E_INVALID_ARG;
-    if (item_weight) *item_weight = ctx->item_overhead;
-    if (prefetch_items) *prefetch_items = ctx->pf_dist;
-    if (static_share) *static_share = ctx->static_frac;
+    const rtbte::LaunchTuning &L = ctx->lt[RTBTE_ALL];
+    if (item_weight) *item_weight = L.w;
+    if (prefetch_items) *prefetch_items = L.pf;
+    if (static_share) *static_share = L.sf;
     return RTBTE_OK;
 }
 

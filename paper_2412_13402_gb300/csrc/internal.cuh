@@ -91,6 +91,15 @@ struct __align__(16) Ctl {
     int cur, last, fixed, pad_i0;
 };
 
+// Launch parameters of the collision kernel for one parts mask.
+struct LaunchTuning {
+    int w = 320;                     // work-split weight of an item beyond its entries
+    int pf = 3;                      // L2 prefetch distance in items of a warp's sequence (0: off)
+    double sf = 1.0;                 // share of the weight split statically (rest: dynamic chunks)
+    double ps[3] = {1.0, 1.0, 1.0};  // relative cost of an entry of each part
+    bool deep = false;               // FP32: the single-buffer form at 24 warps per SM
+};
+
 struct CtlParams {  // constants of one integration (captured into graphs by value)
     double rtol, atol_c, atol_ph;
     double a1, a2, a3, safety, growth, growth_first, etamxf, etamin, hmin, hmax;
@@ -222,16 +231,12 @@ struct rtbte_ctx {
     int part_first[3] = {0, 0, 0};
     int stage_resident = 0;    // stage kernel: blocks resident on the whole GPU at once (its grid)
     int grid = 0, per_sm = 1;  // collision kernel: CTAs per SM (1, 2 or 4; threads = form's threads per SM / per_sm)
-    bool deep[8] = {};         // FP32 launches of parts mask m use the single-buffer 768-thread form
-    unsigned deep_tuned = 0;   // masks whose form the autotuner chose (kept across plans)
+    rtbte::LaunchTuning lt[8];  // collision-kernel launch parameters of each parts mask (1..7)
+    unsigned lt_tuned = 0;      // masks the autotuner tuned themselves (kept across plans)
     std::vector<unsigned short> item_len_h;  // entries per work item (host copy for re-splitting)
     std::vector<int> group_begin_h;          // first item of each group (host copy)
-    int item_overhead = 320;                 // work-split weight of an item beyond its entries
-    double static_frac = 1.0;                // share of the weight split statically (rest: dynamic chunks)
-    int pf_dist = 3;                         // collision kernel: L2 prefetch distance in items
     rtbte::DevBuf tail_tab, tail_ctr;        // dynamic chunks {first, end, group, 0} per mask; grab/exit counters
     int tail_off[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // chunks of mask m: [tail_off[m-1], tail_off[m])
-    double part_scale[3] = {1.0, 1.0, 1.0};  // relative cost of an entry of each part
     size_t smem_bytes = 0;
     bool staged = false;
     bool wide = true;  // every group uses whole-warp items (the kernel variant without sub-warps)
@@ -271,7 +276,7 @@ int make_plan(rtbte_ctx *ctx);
 int launch_prep_from_y(rtbte_ctx *ctx, const double *y, cudaStream_t s);
 int launch_rhs_core(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStream_t s);
 int launch_rows(rtbte_ctx *ctx, unsigned parts, double *out, const double *forcing, cudaStream_t s);
-int split_tables(rtbte_ctx *ctx, int overhead);
+int split_tables(rtbte_ctx *ctx);
 int autotune(rtbte_ctx *ctx, unsigned parts, int *chosen);
 // integrate.cu
 int advance_to(rtbte_ctx *ctx, double t_out, double *y, const rtbte_integ *opt, rtbte_stats *st);

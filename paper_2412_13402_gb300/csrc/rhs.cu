@@ -667,23 +667,21 @@ RowParams row_params(rtbte_ctx *ctx) {
     return Q;
 }
 
-// Per-mask work split of the persistent grid.  Item weight = (entries + `overhead`) x the
-// part's calibrated cost per entry.  The first `static_frac` of a mask's weight is split into
-// equal-weight contiguous CTA ranges (table [mask][grid+1] of real item indices); the rest is
+// Per-mask work split of the persistent grid.  Item weight = (entries + w) x the part's
+// calibrated cost per entry, with each mask's own w and costs.  The first share sf of a mask's
+// weight is split into equal-weight contiguous CTA ranges (table [mask][grid+1] of real item
+// indices); the rest is
 // cut into dynamic chunks of decreasing weight (half the remaining weight per grid, at least
 // 1/40 of a CTA's share, never across a group boundary), taken by CTAs in order at run time.
-int split_tables(rtbte_ctx *ctx, int overhead) {
+int split_tables(rtbte_ctx *ctx) {
     const int G = ctx->grid;
     const std::vector<unsigned short> &len = ctx->item_len_h;
     const int n = (int)len.size();
-    // item weight prefix (all parts), used by the host split below and the device split
-    std::vector<long long> wpre(n + 1, 0);
-    for (int part = 0; part < 3; ++part) {
-        const long long sc = (long long)(64.0 * ctx->part_scale[part] + 0.5);  // cost per entry-equivalent
-        for (int k = ctx->part_first[part]; k < ctx->part_first[part] + ctx->part_items[part]; ++k)
-            wpre[k + 1] = sc * (len[k] + overhead);
-    }
-    for (int k = 0; k < n; ++k) wpre[k + 1] += wpre[k];
+    // weight of item k under mask m's parameters: (entries + w) x the part's cost per entry
+    auto weight = [&](const LaunchTuning &L, int part, int k) {
+        const long long sc = (long long)(64.0 * L.ps[part] + 0.5);  // cost per entry-equivalent
+        return sc * (len[k] + L.w);
+    };
     std::vector<int> item_group(n, 0);
     for (size_t g = 0; g < ctx->group_begin_h.size(); ++g) {
         const int e = g + 1 < ctx->group_begin_h.size() ? ctx->group_begin_h[g + 1] : n;
@@ -694,18 +692,19 @@ int split_tables(rtbte_ctx *ctx, int overhead) {
     std::vector<long long> apre;  // prefix of the enabled parts' weights, item order
     std::vector<int> aidx;
     for (unsigned mask = 1; mask <= 7; ++mask) {
+        const LaunchTuning &L = ctx->lt[mask];
         apre.assign(1, 0);
         aidx.clear();
         for (int part = 0; part < 3; ++part) {
             if (!(mask & (1u << part))) continue;
             for (int k = ctx->part_first[part]; k < ctx->part_first[part] + ctx->part_items[part]; ++k) {
-                apre.push_back(apre.back() + (wpre[k + 1] - wpre[k]));
+                apre.push_back(apre.back() + weight(L, part, k));
                 aidx.push_back(k);
             }
         }
         const long long total = apre.back();
         const int na = (int)aidx.size();
-        const long long split = ctx->static_frac >= 1.0 ? total : (long long)(ctx->static_frac * (double)total);
+        const long long split = L.sf >= 1.0 ? total : (long long)(L.sf * (double)total);
         const int js = (int)(std::lower_bound(apre.begin(), apre.end(), split) - apre.begin());  // first tail item
         int *t = tab.data() + (long long)(mask - 1) * (G + 1);
         for (int c = 0; c <= G; ++c) {
@@ -734,7 +733,12 @@ int split_tables(rtbte_ctx *ctx, int overhead) {
         }
         ctx->tail_off[mask] = (int)tail.size();
     }
-    ctx->item_overhead = overhead;
+    // per-group weights for the device re-split of batched integrations (full-RHS parameters)
+    std::vector<long long> wpre(n + 1, 0);
+    for (int part = 0; part < 3; ++part)
+        for (int k = ctx->part_first[part]; k < ctx->part_first[part] + ctx->part_items[part]; ++k)
+            wpre[k + 1] = weight(ctx->lt[7], part, k);
+    for (int k = 0; k < n; ++k) wpre[k + 1] += wpre[k];
     std::vector<long long> gwt(ctx->group_begin_h.size());  // weight of each group's items
     for (size_t g = 0; g < gwt.size(); ++g) {
         const int e = g + 1 < ctx->group_begin_h.size() ? ctx->group_begin_h[g + 1] : n;
@@ -958,7 +962,7 @@ int make_plan(rtbte_ctx *ctx) {
     }
     ctx->per_sm = per_sm;
     for (unsigned m = 0; m < 8; ++m)  // default: the 768-thread form where e-ph work is in the launch
-        if (!(ctx->deep_tuned & (1u << m))) ctx->deep[m] = !fp64 && (m & (1u << PART_EPH));
+        if (!(ctx->lt_tuned & (1u << m))) ctx->lt[m].deep = !fp64 && (m & (1u << PART_EPH));
     ctx->grid = ctx->num_sms * (ctx->staged ? per_sm : 2);
     ctx->item_len_h.resize(items.size());
     for (size_t k = 0; k < items.size(); ++k) ctx->item_len_h[k] = items[k].len;
@@ -984,7 +988,7 @@ int make_plan(rtbte_ctx *ctx) {
         for (const InstHost &I : ctx->inst) nrb += (I.d.n_c + I.n_ph + 255) / 256;
     ctx->n_rblk = (int)nrb;
     ctx->dyn_tab.release();  // reallocated below for this plan's sizes
-    if ((rc = split_tables(ctx, ctx->item_overhead))) return rc;
+    if ((rc = split_tables(ctx))) return rc;
     if (ctx->n_groups > 1024) return fail(ctx, RTBTE_E_UNSUPPORTED, "more than 1024 staging groups");
     // device re-split tables: [grid+1] item bounds, [grid] act indices, [n_groups+1] active groups,
     // then the memo of the last split: [n_inst] done flags it saw, its parts mask, a valid flag
@@ -1024,7 +1028,7 @@ static int launch_core_t(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStr
     P.groups = ctx->groups.as<Group>();
     P.n_groups = ctx->n_groups;
     P.mask = parts;
-    P.pf_dist = ctx->pf_dist;
+    P.pf_dist = ctx->lt[parts].pf;
     if (ctl && ctx->inst.size() > 1) {  // batched integration: balance over the active instances
         int *dt = ctx->dyn_tab.as<int>();  // [grid+1] item bounds, [grid] act indices, [n_groups+1] act, memo
         split_kernel<<<1, 256, 0, s>>>(ctx->groups.as<Group>(), ctx->n_groups, ctx->gwt.as<long long>(), ctl, parts,
@@ -1066,7 +1070,7 @@ static int launch_core_t(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStr
     if (!ctx->staged) {
         rhs_kernel<R, false, false, false, 2, kRhsThreads><<<ctx->grid, kRhsThreads, 0, s>>>(P);
     } else if constexpr (sizeof(R) == 4) {
-        if (ctx->deep[parts]) {
+        if (ctx->lt[parts].deep) {
             const int nt = kRhsThreadsDeep / ctx->per_sm;
             if (ctx->wide)
                 rhs_kernel<R, true, false, true, 1, kRhsThreadsDeep><<<ctx->grid, nt, ctx->smem_bytes, s>>>(P);
@@ -1116,34 +1120,44 @@ int time_launches(rtbte_ctx *ctx, unsigned parts, cudaEvent_t e0, cudaEvent_t e1
     return RTBTE_OK;
 }
 
-// Tuning of the work split for the current kernel form: per-item weight, per-part entry costs,
-// L2 prefetch distance and static share, each timed over 3 launches and the fastest kept.
-int tune_split(rtbte_ctx *ctx, unsigned parts, cudaEvent_t e0, cudaEvent_t e1, int *chosen) {
+// Tuning of mask `parts`'s work split for its current kernel form: per-item weight, per-part
+// entry costs, L2 prefetch distance and static share, each timed over 3 launches and the
+// fastest kept.
+int tune_split(rtbte_ctx *ctx, unsigned parts, cudaEvent_t e0, cudaEvent_t e1) {
     static const int cand[] = {32, 96, 192, 320, 512, 800, 1280, 2048};
-    int best = ctx->item_overhead, rc = RTBTE_OK;
+    LaunchTuning &L = ctx->lt[parts];
+    int best = L.w, rc = RTBTE_OK;
     float best_ms = 1e30f;
     for (int w : cand) {
         float ms = 0.f;
-        if ((rc = split_tables(ctx, w)) || (rc = time_launches(ctx, parts, e0, e1, 3, &ms))) return rc;
+        L.w = w;
+        if ((rc = split_tables(ctx)) || (rc = time_launches(ctx, parts, e0, e1, 3, &ms))) return rc;
         if (ms < best_ms) {
             best_ms = ms;
             best = w;
         }
     }
-    if ((rc = split_tables(ctx, best))) return rc;
-    // calibrate the relative cost of an entry in each part from single-part launches, keep it
-    // if the combined launch gets faster
-    const double scale0[3] = {ctx->part_scale[0], ctx->part_scale[1], ctx->part_scale[2]};
+    L.w = best;
+    if ((rc = split_tables(ctx))) return rc;
+    // calibrate the relative cost of an entry in each part from single-part launches (run with
+    // this mask's parameters), keep it if this mask's launch gets faster
+    const double scale0[3] = {L.ps[0], L.ps[1], L.ps[2]};
     double t[3] = {0, 0, 0}, wsum[3] = {0, 0, 0};
     int used = 0;
     for (int part = 0; part < 3; ++part) {
-        if (!(parts & (1u << part)) || ctx->part_items[part] == 0) continue;
+        if (!(parts & (1u << part)) || ctx->part_items[part] == 0 || (parts == (1u << part))) continue;
         for (int k = ctx->part_first[part]; k < ctx->part_first[part] + ctx->part_items[part]; ++k)
             wsum[part] += ctx->item_len_h[k] + best;
+        const unsigned pm = 1u << part;
+        const LaunchTuning keep = ctx->lt[pm];
+        ctx->lt[pm] = L;
         float ms = 0.f;
-        if ((rc = time_launches(ctx, 1u << part, e0, e1, 3, &ms))) return rc;
+        rc = split_tables(ctx);
+        if (!rc) rc = time_launches(ctx, pm, e0, e1, 3, &ms);
+        ctx->lt[pm] = keep;
+        if (rc) return rc;
         t[part] = ms;
-        used |= 1u << part;
+        used |= pm;
     }
     if (used) {
         double ref = 0.0;
@@ -1155,21 +1169,21 @@ int tune_split(rtbte_ctx *ctx, unsigned parts, cudaEvent_t e0, cudaEvent_t e1, i
             }
         ref /= nref;
         for (int part = 0; part < 3; ++part)
-            if (used & (1u << part)) ctx->part_scale[part] = (t[part] / wsum[part]) / ref;
+            if (used & (1u << part)) L.ps[part] = (t[part] / wsum[part]) / ref;
         float ms = 0.f;
-        if ((rc = split_tables(ctx, best)) || (rc = time_launches(ctx, parts, e0, e1, 3, &ms))) return rc;
-        if (ms > best_ms) {  // calibration did not help: back to uniform costs
-            for (int part = 0; part < 3; ++part) ctx->part_scale[part] = scale0[part];
-            if ((rc = split_tables(ctx, best))) return rc;
+        if ((rc = split_tables(ctx)) || (rc = time_launches(ctx, parts, e0, e1, 3, &ms))) return rc;
+        if (ms > best_ms) {  // calibration did not help: back to the previous costs
+            for (int part = 0; part < 3; ++part) L.ps[part] = scale0[part];
+            if ((rc = split_tables(ctx))) return rc;
         }
     }
     // L2 prefetch distance, then the share of the work split statically (the rest is taken
     // dynamically by CTAs that finish early)
     static const int dists[] = {0, 2, 3, 4, 6, 8};
-    int best_d = ctx->pf_dist;
+    int best_d = L.pf;
     float best_d_ms = 1e30f;
     for (int d : dists) {
-        ctx->pf_dist = d;
+        L.pf = d;
         float ms = 0.f;
         if ((rc = time_launches(ctx, parts, e0, e1, 3, &ms))) return rc;
         if (ms < best_d_ms) {
@@ -1177,77 +1191,64 @@ int tune_split(rtbte_ctx *ctx, unsigned parts, cudaEvent_t e0, cudaEvent_t e1, i
             best_d = d;
         }
     }
-    ctx->pf_dist = best_d;
+    L.pf = best_d;
     static const double fracs[] = {1.0, 0.9, 0.8, 0.7, 0.6};
     double best_f = 1.0;
     float best_f_ms = 1e30f;
     for (double f : fracs) {
-        ctx->static_frac = f;
+        L.sf = f;
         float ms = 0.f;
-        if ((rc = split_tables(ctx, best)) || (rc = time_launches(ctx, parts, e0, e1, 3, &ms))) return rc;
+        if ((rc = split_tables(ctx)) || (rc = time_launches(ctx, parts, e0, e1, 3, &ms))) return rc;
         if (ms < best_f_ms) {
             best_f_ms = ms;
             best_f = f;
         }
     }
-    ctx->static_frac = best_f;
-    *chosen = best;
-    return split_tables(ctx, best);
+    L.sf = best_f;
+    return split_tables(ctx);
 }
 
 }  // namespace
 
-// Autotuner of the collision launch.  FP32 has two kernel forms (two entry buffers per warp at
-// 16 warps per SM, or one buffer at 24): the work split is tuned for each form from the same
-// starting point, the two tuned launches are timed over 10 launches each (they often differ by
-// ~2%, less than the spread of 3-launch timings) and the faster is kept for this parts mask.
+// Autotuner of the collision launch of one parts mask.  FP32 has two kernel forms (two entry
+// buffers per warp at 16 warps per SM, or one buffer at 24): the work split is tuned for each
+// form from the same starting point, the two tuned launches are timed over 10 launches each
+// (they often differ by ~2%, less than the spread of 3-launch timings) and the faster is kept.
+// The result belongs to this mask; masks never tuned themselves take its work split (not its
+// form) as their own.
 int autotune(rtbte_ctx *ctx, unsigned parts, int *chosen) {
     cudaEvent_t e0, e1;
     RT_CUDA(ctx, cudaEventCreate(&e0));
     RT_CUDA(ctx, cudaEventCreate(&e1));
-    struct Tuned {
-        int w, pf;
-        double sf, ps[3];
-        float ms;
-    };
-    auto save = [&](int w, float ms) {
-        return Tuned{w, ctx->pf_dist, ctx->static_frac, {ctx->part_scale[0], ctx->part_scale[1], ctx->part_scale[2]}, ms};
-    };
-    auto load = [&](const Tuned &T) {
-        ctx->pf_dist = T.pf;
-        ctx->static_frac = T.sf;
-        for (int p = 0; p < 3; ++p) ctx->part_scale[p] = T.ps[p];
-        return split_tables(ctx, T.w);
-    };
     const bool two_forms = ctx->staged && ctx->precision != RTBTE_PREC_FP64;
-    const bool deep0 = ctx->deep[parts];
-    const Tuned start = save(ctx->item_overhead, 0.f);
-    Tuned res[2] = {start, start};
+    const LaunchTuning start = ctx->lt[parts];
+    LaunchTuning res[2] = {start, start};
+    float ms10[2] = {0.f, 0.f};
     int rc = RTBTE_OK, nf = two_forms ? 2 : 1;
     for (int f = 0; f < nf && !rc; ++f) {
-        if (two_forms) ctx->deep[parts] = f == 1;
-        int w = start.w;
-        float ms = 0.f;
-        if ((rc = load(start)) || (rc = tune_split(ctx, parts, e0, e1, &w))) break;
-        if (two_forms && (rc = time_launches(ctx, parts, e0, e1, 10, &ms))) break;
-        res[f] = save(w, ms);
+        ctx->lt[parts] = start;
+        if (two_forms) ctx->lt[parts].deep = f == 1;
+        if ((rc = tune_split(ctx, parts, e0, e1))) break;
+        if (two_forms && (rc = time_launches(ctx, parts, e0, e1, 10, &ms10[f]))) break;
+        res[f] = ctx->lt[parts];
     }
-    int pick = 0;
-    if (!rc && two_forms) {
-        pick = res[1].ms < res[0].ms ? 1 : 0;
-        ctx->deep[parts] = pick == 1;
-        ctx->deep_tuned |= 1u << parts;
+    const int pick = (!rc && two_forms && ms10[1] < ms10[0]) ? 1 : 0;
+    ctx->lt[parts] = rc ? start : res[pick];
+    if (!rc) {
+        ctx->lt_tuned |= 1u << parts;
+        for (unsigned m = 1; m <= 7; ++m) {
+            if (m == parts || (ctx->lt_tuned & (1u << m))) continue;
+            const bool deep = ctx->lt[m].deep;
+            ctx->lt[m] = ctx->lt[parts];
+            ctx->lt[m].deep = deep;
+        }
     }
-    if (rc) {  // back to the starting launch parameters
-        ctx->deep[parts] = deep0;
-        load(start);
-    } else {
-        rc = load(res[pick]);
-    }
+    const int rc2 = split_tables(ctx);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    if (chosen) *chosen = res[pick].w;
+    if (rc2) return rc2;
+    if (chosen) *chosen = ctx->lt[parts].w;
     return RTBTE_OK;
 }
 

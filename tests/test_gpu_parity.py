@@ -176,6 +176,24 @@ def test_autotune_keeps_results_bitwise(rt):
     ctx.close()
 
 
+def test_per_mask_tuning_is_kept_per_mask(rt):
+    """Tuning the fast and slow masks of MRI leaves the full-RHS launch parameters as they were,
+    and no tuning changes any result bit."""
+    m = ri.graphene_small(36)
+    ctx = rt.Context(m)
+    ctx.upload_channels()
+    y = torch.tensor(sym_state(m, 9), device="cuda")
+    before = {p: ctx.rhs(y, parts=p).cpu().numpy() for p in (ALL, FAST, SLOW)}
+    ctx.autotune(ALL)
+    t_all = ctx.tuning()
+    ctx.autotune(FAST)
+    ctx.autotune(SLOW)
+    assert ctx.tuning() == t_all
+    for p, b in before.items():
+        assert np.array_equal(ctx.rhs(y, parts=p).cpu().numpy(), b)
+    ctx.close()
+
+
 @pytest.mark.parametrize("which", ["wide", "sub-warp"])
 def test_fp32_launch_forms_agree_bitwise(rt, which):
     """The two FP32 launch forms (two entry buffers per warp at 16 warps per SM; one buffer at

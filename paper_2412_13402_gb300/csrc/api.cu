@@ -748,7 +748,7 @@ void rtbte_destroy(rtbte_ctx *ctx) {
     ctx->tail_tab.release();
     ctx->tail_ctr.release();
     DevBuf *bufs[] = {&ctx->popf, &ctx->popN, &ctx->popP, &ctx->instdev, &ctx->compact, &ctx->items, &ctx->groups,
-                      &ctx->partials, &ctx->eoff, &ctx->poff, &ctx->ppoff, &ctx->cta_tab, &ctx->gwt, &ctx->dyn_tab, &ctx->Y[0], &ctx->Y[1],
+                      &ctx->partials, &ctx->rowoff, &ctx->rowmid, &ctx->cta_tab, &ctx->gwt, &ctx->dyn_tab, &ctx->Y[0], &ctx->Y[1],
                       &ctx->K, &ctx->Fs, &ctx->forcing, &ctx->wrms_part, &ctx->ctl, &ctx->ystage, &ctx->ydstage,
                       &ctx->range_scratch, &ctx->slow_save};
     for (DevBuf *b : bufs) b->release();

@@ -45,12 +45,24 @@ enum { PART_EPH = 0, PART_PHE = 1, PART_PP = 2 };
 // one warp while groups of long segments keep whole-warp items.
 
 
-struct __align__(16) Item {
-    long long begin;      // first entry, relative to the group's entry arrays
-    int dest;             // instance-local destination (electron d, phonon p, sub-lattice a)
-    unsigned short len;   // entries (multiple of 4, <= kItemEntries)
-    unsigned char proc;   // 0 emission, 1 absorption
-    unsigned char pad;
+// A work item as stored (16 B): up to kItemEntries entries of one destination segment.
+struct __align__(16) ItemRec {
+    unsigned int begin_lo;   // first entry (bits 0-31), relative to the group's entry arrays
+    unsigned int slot;       // index of the item's partial: the items of one row have consecutive
+                             // slots, in the order the row adds them
+    int dest;                // instance-local destination (electron d, phonon p, sub-lattice a)
+    unsigned short len;      // entries (multiple of 4, <= kItemEntries)
+    unsigned char proc;      // 0 emission, 1 absorption
+    unsigned char begin_hi;  // first entry, bits 32-39
+};
+
+// A work item as the collision kernel uses it.
+struct Item {
+    long long begin;
+    unsigned int slot;
+    int dest;
+    unsigned short len;
+    unsigned char proc;
 };
 
 // Consecutive items that share one shared-memory staging of populations.
@@ -72,11 +84,8 @@ struct __align__(16) Group {
 struct __align__(16) InstDev {
     long long y_off;
     int n_c, n_ph, M, nmodes;
-    int N_q, N_q_pad, eblocks, pad1;  // eblocks: e-ph item-offset blocks (modes x q-blocks)
+    int N_q, N_q_pad;
     long long f_off, N_off, P_off;  // offsets in popf / popN / popP
-    long long eoff_base;            // item offsets of e-ph rows: [nmodes][n_c+1]
-    long long poff_base;            // item offsets of ph-e rows: [n_ph+1]
-    long long ppoff_base;           // item offsets of ph-ph rows: [M+1]
     long long compact_base;         // sub-lattice index of each phonon (-1: none): [n_ph]
 };
 
@@ -224,7 +233,7 @@ struct rtbte_ctx {
     rtbte::DevBuf popf, popN, popP, instdev, compact;
     // execution plan of the RHS
     bool plan_valid = false;
-    rtbte::DevBuf items, groups, partials, eoff, poff, ppoff, cta_tab, gwt, dyn_tab;
+    rtbte::DevBuf items, groups, partials, rowoff, rowmid, cta_tab, gwt, dyn_tab;  // rowoff/rowmid: slots of each row
     int n_rblk = 0;  // several instances: row blocks of the stage kernels (256 rows of one instance each)
     int n_items = 0, n_groups = 0;
     int part_items[3] = {0, 0, 0};

@@ -11,7 +11,8 @@
 // 512 entries, groups of short ones give each sub-warp of 4, 8 or 16 lanes one item of up to 64,
 // 128 or 256 entries.  Lanes accumulate their entries with
 // compensated (two-sum) additions and adds the lanes with a shuffle tree; the partial is
-// written per item, and the row kernels add partials in item order (deterministic).  CTAs
+// written per item to the item's slot -- the slots of one row's items are consecutive -- and
+// the row kernels add a row's partials in slot order (deterministic).  CTAs
 // first run a static share of the items (split by estimated cost), then take the rest in
 // chunks from a counter; warps may prefetch upcoming items' entries into L2.  FP32 launches
 // come in two forms, chosen per parts mask: two register buffers of entries per warp (the next
@@ -49,7 +50,7 @@ template <class R> __device__ __forceinline__ void two_sum(R &s, R &c, R x) {
 }
 
 struct KParams {
-    const Item *items;
+    const ItemRec *items;
     const Group *groups;
     int n_groups;
     const int *cta_items;  // [grid+1] first item of each CTA's static range (real item indices)
@@ -231,13 +232,13 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
     }
 }
 
-__device__ __forceinline__ Item item_from(const int4 &d) {
+__device__ __forceinline__ Item item_from(const int4 &d) {  // decode an ItemRec
     Item it;
-    it.begin = ((long long)(unsigned)d.y << 32) | (unsigned)d.x;
+    it.begin = ((long long)((unsigned)d.w >> 24) << 32) | (unsigned)d.x;
+    it.slot = (unsigned)d.y;
     it.dest = d.z;
     it.len = (unsigned short)(d.w & 0xffff);
     it.proc = (unsigned char)((d.w >> 16) & 0xff);
-    it.pad = 0;
     return it;
 }
 
@@ -251,7 +252,7 @@ struct DescStream {
         const int k = base + lane * stride;
         return k < end ? __ldg(items + k) : make_int4(0, 0, 0, 0);
     }
-    __device__ __forceinline__ void init(const Item *it, int a, int b, int st, int lane) {
+    __device__ __forceinline__ void init(const ItemRec *it, int a, int b, int st, int lane) {
         items = reinterpret_cast<const int4 *>(it);
         k0 = a;
         end = b;
@@ -325,14 +326,14 @@ __device__ __forceinline__ void prefetch_item(const GroupView<R> &V, const DescS
 // is set by the conversion of the populations to FP32 (about 5e-8 relative on the parity
 // models), not by this tree: the compensated tree measured the same to two digits.
 template <class R>
-__device__ __forceinline__ void finish_item(const KParams &P, int k, bool valid, R acc, R cmp, int sl, int lg) {
+__device__ __forceinline__ void finish_item(const KParams &P, unsigned slot, bool valid, R acc, R cmp, int sl, int lg) {
     acc += cmp;
     cmp = R(0);
 #pragma unroll
     for (int o = 16; o; o >>= 1)
         if (o < (1 << lg)) acc += __shfl_xor_sync(kFull, acc, o);
     if (sl == 0 && valid) {
-        R *out = reinterpret_cast<R *>(P.partials) + 2LL * k;
+        R *out = reinterpret_cast<R *>(P.partials) + 2LL * slot;
         out[0] = acc;
         out[1] = cmp;
     }
@@ -365,7 +366,7 @@ __device__ __forceinline__ void run_range(const KParams &P, const GroupView<R> &
             Batch<R, 4> B;
             B.issue(V, it, sl, lg);
             compute_item<R, 4>(V, it, B, sl, lg, acc, cmp);
-            finish_item<R>(P, k + h * st, valid(k), acc, cmp, sl, lg);
+            finish_item<R>(P, it.slot, valid(k), acc, cmp, sl, lg);
         }
         return;
     }
@@ -382,7 +383,7 @@ __device__ __forceinline__ void run_range(const KParams &P, const GroupView<R> &
         }
         if (pf > 0) prefetch_item(V, D, k + pf * G * st, b, lane);
         compute_item<R, 4>(V, ia, A, sl, lg, acc, cmp);
-        finish_item<R>(P, k + h * st, valid(k), acc, cmp, sl, lg);
+        finish_item<R>(P, ia.slot, valid(k), acc, cmp, sl, lg);
         if (!hb) break;
         k += G * st;
         const bool ha = k + G * st < b;
@@ -392,7 +393,7 @@ __device__ __forceinline__ void run_range(const KParams &P, const GroupView<R> &
         }
         if (pf > 0) prefetch_item(V, D, k + pf * G * st, b, lane);
         compute_item<R, 4>(V, ib, B, sl, lg, acc, cmp);
-        finish_item<R>(P, k + h * st, valid(k), acc, cmp, sl, lg);
+        finish_item<R>(P, ib.slot, valid(k), acc, cmp, sl, lg);
         if (!ha) break;
         k += G * st;
     }
@@ -656,9 +657,8 @@ RowParams row_params(rtbte_ctx *ctx) {
     RowParams Q;
     Q.inst = ctx->instdev.as<InstDev>();
     Q.n_inst = (int)ctx->inst.size();
-    Q.eoff = ctx->eoff.as<int>();
-    Q.poff = ctx->poff.as<int>();
-    Q.ppoff = ctx->ppoff.as<int>();
+    Q.rowoff = ctx->rowoff.as<int>();
+    Q.rowmid = ctx->rowmid.as<int>();
     Q.compact = ctx->compact.as<int>();
     Q.partials = ctx->partials.p;
     Q.popf = ctx->popf.p;
@@ -755,13 +755,15 @@ int split_tables(rtbte_ctx *ctx) {
     return upload_vec(ctx, ctx->cta_tab, tab);
 }
 
-// Build the work items, staging groups, per-row item offsets and per-CTA work ranges.
+// Build the work items, staging groups, per-row partial slots and per-CTA work ranges.
 int make_plan(rtbte_ctx *ctx) {
     const size_t R = ctx->real_size;
-    std::vector<Item> items;
+    std::vector<ItemRec> items;
     std::vector<Group> groups;
-    std::vector<int> eoff, poff, ppoff;
+    std::vector<int> eoff, poff, ppoff;  // item offsets per row (host only: they order the slots)
+    std::vector<long long> eoff_base(ctx->inst.size()), poff_base(ctx->inst.size()), ppoff_base(ctx->inst.size());
     std::vector<InstDev> idev(ctx->inst.size());
+    bool begin_overflow = false;
     int cut = 512;  // entries per item at most (16 << the current group's lanes_log2)
     // lanes per item of a group: from the mean padded length of its non-empty segments [s0, s1),
     // counted over every row (also those outside a row slice, so that a sliced context cuts
@@ -778,12 +780,14 @@ int make_plan(rtbte_ctx *ctx) {
     };
     auto add_seg = [&](long long b, long long e, int dest, int proc) {
         for (long long x = b; x < e; x += cut) {
-            Item it;
-            it.begin = x;
+            ItemRec it;
+            begin_overflow = begin_overflow || x >= (1LL << 40);
+            it.begin_lo = (unsigned)(x & 0xffffffffLL);
+            it.begin_hi = (unsigned char)((x >> 32) & 0xff);
+            it.slot = 0;  // set once every item exists
             it.dest = dest;
             it.len = (unsigned short)std::min<long long>(cut, e - x);
             it.proc = (unsigned char)proc;
-            it.pad = 0;
             items.push_back(it);
         }
     };
@@ -791,7 +795,7 @@ int make_plan(rtbte_ctx *ctx) {
     // e-ph groups (instance, mode)
     for (size_t i = 0; i < ctx->inst.size(); ++i) {
         InstHost &I = ctx->inst[i];
-        idev[i].eoff_base = (long long)eoff.size();
+        eoff_base[i] = (long long)eoff.size();
         const int nqb = std::max(I.eph_nqb, 1);
         const int qblk = I.eph_qblk > 0 ? I.eph_qblk : I.N_q_pad;
         for (int blk = 0; blk < I.d.nmodes * nqb; ++blk) {  // (mode, q-block)
@@ -834,7 +838,7 @@ int make_plan(rtbte_ctx *ctx) {
     // ph-e groups (instance)
     for (size_t i = 0; i < ctx->inst.size(); ++i) {
         InstHost &I = ctx->inst[i];
-        idev[i].poff_base = (long long)poff.size();
+        poff_base[i] = (long long)poff.size();
         Group G{};
         G.idx = I.phe_idx.as<uint32_t>();
         G.W = I.phe_W.p;
@@ -867,7 +871,7 @@ int make_plan(rtbte_ctx *ctx) {
     // ph-ph groups (instance)
     for (size_t i = 0; i < ctx->inst.size(); ++i) {
         InstHost &I = ctx->inst[i];
-        idev[i].ppoff_base = (long long)ppoff.size();
+        ppoff_base[i] = (long long)ppoff.size();
         if (I.M == 0) continue;
         Group G{};
         G.idx = I.pp_idx.as<uint32_t>();
@@ -897,6 +901,41 @@ int make_plan(rtbte_ctx *ctx) {
     ctx->part_first[PART_PP] = ctx->part_first[PART_PHE] + ctx->part_items[PART_PHE];
     ctx->part_items[PART_PP] = (int)items.size() - ctx->part_first[PART_PP];
     if (items.size() >= (size_t)INT32_MAX) return fail(ctx, RTBTE_E_UNSUPPORTED, "too many work items");
+    if (begin_overflow) return fail(ctx, RTBTE_E_UNSUPPORTED, "channel list longer than 2^40 entries");
+    // partial slots, row-major: every row's items get consecutive slots in the order the row
+    // adds them (an electron row: its (mode, q-block) blocks in turn, emission then absorption
+    // items of each; a phonon row: its ph-e items, then its ph-ph items if it is a sub-lattice
+    // phonon), so a row kernel reads one offset pair and one contiguous run of partials
+    std::vector<int> rowoff(ctx->n_y + 1, 0), rowmid(std::max<long long>(ctx->n_y, 1), 0);
+    {
+        long long next = 0;
+        auto take = [&](int i0, int i1) {
+            for (int k = i0; k < i1; ++k) items[k].slot = (unsigned)next++;
+        };
+        for (size_t i = 0; i < ctx->inst.size(); ++i) {
+            const InstHost &I = ctx->inst[i];
+            const int nc = I.d.n_c, nblk = I.d.nmodes * std::max(I.eph_nqb, 1);
+            for (int d = 0; d < nc; ++d) {
+                const long long c = I.y_off + d;
+                rowoff[c] = (int)next;
+                for (int blk = 0; blk < nblk; ++blk) {
+                    const long long o = eoff_base[i] + (long long)blk * (nc + 1) + d;
+                    take(eoff[o], eoff[o + 1]);
+                }
+                rowmid[c] = (int)next;
+            }
+            for (long long p = 0; p < I.n_ph; ++p) {
+                const long long c = I.y_off + nc + p;
+                rowoff[c] = (int)next;
+                take(poff[poff_base[i] + p], poff[poff_base[i] + p + 1]);
+                rowmid[c] = (int)next;
+                const int a = I.M > 0 ? I.compact[p] : -1;
+                if (a >= 0) take(ppoff[ppoff_base[i] + a], ppoff[ppoff_base[i] + a + 1]);
+            }
+        }
+        rowoff[ctx->n_y] = (int)next;
+        if (next != (long long)items.size()) return fail(ctx, RTBTE_E_UNSUPPORTED, "work items not covered by rows");
+    }
     ctx->n_items = (int)items.size();
     ctx->n_groups = (int)groups.size();
     ctx->wide = std::all_of(groups.begin(), groups.end(), [](const Group &G) { return G.lanes_log2 == 5; });
@@ -912,7 +951,6 @@ int make_plan(rtbte_ctx *ctx) {
         D.nmodes = I.d.nmodes;
         D.N_q = (int)I.N_q;
         D.N_q_pad = I.N_q_pad;
-        D.eblocks = I.d.nmodes * std::max(I.eph_nqb, 1);
         D.f_off = I.f_off;
         D.N_off = I.N_off;
         D.P_off = I.P_off;
@@ -976,9 +1014,8 @@ int make_plan(rtbte_ctx *ctx) {
     }
     if ((rc = upload_vec(ctx, ctx->items, items))) return rc;
     if ((rc = upload_vec(ctx, ctx->groups, groups))) return rc;
-    if ((rc = upload_vec(ctx, ctx->eoff, eoff))) return rc;
-    if ((rc = upload_vec(ctx, ctx->poff, poff))) return rc;
-    if ((rc = upload_vec(ctx, ctx->ppoff, ppoff))) return rc;
+    if ((rc = upload_vec(ctx, ctx->rowoff, rowoff))) return rc;
+    if ((rc = upload_vec(ctx, ctx->rowmid, rowmid))) return rc;
     if ((rc = upload_vec(ctx, ctx->instdev, idev))) return rc;
     if ((rc = upload_vec(ctx, ctx->compact, compact))) return rc;
     if (ctx->n_y >= (long long)INT32_MAX) return fail(ctx, RTBTE_E_UNSUPPORTED, "state vector too long");
@@ -1024,7 +1061,7 @@ template <class R>
 static int launch_core_t(rtbte_ctx *ctx, unsigned parts, const Ctl *ctl, cudaStream_t s) {
     KParams P;
     std::memset(&P, 0, sizeof(P));
-    P.items = ctx->items.as<Item>();
+    P.items = ctx->items.as<ItemRec>();
     P.groups = ctx->groups.as<Group>();
     P.n_groups = ctx->n_groups;
     P.mask = parts;

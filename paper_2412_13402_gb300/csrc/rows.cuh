@@ -13,7 +13,8 @@ namespace rtbte {
 struct RowParams {
     const InstDev *inst;
     int n_inst;
-    const int *eoff, *poff, *ppoff;  // item offsets per row (absolute item ids)
+    const int *rowoff;               // [n_y+1] first partial slot of each state row
+    const int *rowmid;               // [n_y] phonon rows: first ph-ph slot (ph-e slots before it)
     const int *compact;              // sub-lattice index of each phonon or -1
     const void *partials;            // (hi, lo) per item, compute precision
     void *popf, *popN, *popP;        // population copies, compute precision
@@ -54,31 +55,21 @@ __device__ __forceinline__ void item_sum(const RowParams &Q, int i0, int i1, Row
     for (int it = i0; it < i1; ++it) A.add(P[2 * it], P[2 * it + 1]);
 }
 
-// RHS value of row `local` of instance I for the selected parts.
+// RHS value of row `local` of instance I for the selected parts.  The row's partials sit in
+// consecutive slots: an electron row's e-ph items in (mode, q-block) order, a phonon row's ph-e
+// items then its ph-ph items (sub-lattice phonons only).
 template <class R>
 __device__ __forceinline__ double row_value(const RowParams &Q, const InstDev &I, long long local, unsigned parts) {
+    const long long c = I.y_off + local;
+    const int s0 = Q.rowoff[c], s1 = Q.rowmid[c], s2 = Q.rowoff[c + 1];
     RowAcc<R> A;
     if (local < I.n_c) {
         if (!(parts & RTBTE_EPH)) return 0.0;
-        const int d = (int)local;
-        for (int blk = 0; blk < I.eblocks; ++blk) {  // (mode, q-block) blocks of item offsets
-            const int *o = Q.eoff + I.eoff_base + (long long)blk * (I.n_c + 1);
-            item_sum<R>(Q, o[d], o[d + 1], A);
-        }
+        item_sum<R>(Q, s0, s2, A);
         return -A.value();
     }
-    const long long p = local - I.n_c;
-    if (parts & RTBTE_PHE) {
-        const int *o = Q.poff + I.poff_base;
-        item_sum<R>(Q, o[p], o[p + 1], A);
-    }
-    if ((parts & RTBTE_PHPH) && I.M > 0) {
-        const int a = Q.compact[I.compact_base + p];
-        if (a >= 0) {
-            const int *o = Q.ppoff + I.ppoff_base;
-            item_sum<R>(Q, o[a], o[a + 1], A);
-        }
-    }
+    if (parts & RTBTE_PHE) item_sum<R>(Q, s0, s1, A);
+    if (parts & RTBTE_PHPH) item_sum<R>(Q, s1, s2, A);
     return -A.value();
 }
 

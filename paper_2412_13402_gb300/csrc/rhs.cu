@@ -10,7 +10,8 @@
 // of a single destination segment; groups of long segments give each warp one item of up to
 // 512 entries, groups of short ones give each sub-warp of 4, 8 or 16 lanes one item of up to 64,
 // 128 or 256 entries.  Lanes accumulate their entries with
-// compensated (two-sum) additions and adds the lanes with a shuffle tree; the partial is
+// compensated (two-sum) additions in FP32, plain ones in FP64, and add the lanes with a shuffle
+// tree; the partial is
 // written per item to the item's slot -- the slots of one row's items are consecutive -- and
 // the row kernels add a row's partials in slot order (deterministic).  CTAs
 // first run a static share of the items (split by estimated cost), then take the rest in
@@ -47,6 +48,14 @@ template <class R> __device__ __forceinline__ void two_sum(R &s, R &c, R x) {
     R e = (s - (t - bp)) + (x - bp);
     s = t;
     c += e;
+}
+
+// A lane's sum of its (at most 4) vector sums within an item: compensated in FP32; a plain
+// addition in FP64, whose rounding over 4 terms is far below the FP64 study's needs and whose
+// arithmetic this GPU runs at a low rate (the compensated form cost FP64 mode ~20% of its time).
+template <class R> __device__ __forceinline__ void lane_add(R &s, R &c, R x) {
+    if constexpr (sizeof(R) == 8) s += x;
+    else two_sum(s, c, x);
 }
 
 struct KParams {
@@ -140,8 +149,7 @@ __device__ __forceinline__ unsigned comp4(const uint4 &e, int k) {
 }
 
 // Per-lane sum of W*F over one item: each 4-entry vector is summed with an FMA chain and the
-// vector sums are added with two-sum into (acc, cmp); the warp reduction is done later for
-// four items at once (Pending).
+// vector sums are added into (acc, cmp) by lane_add; the warp reduction follows in finish_item.
 template <class R, int VPL>
 __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &it, const Batch<R, VPL> &b, int sl,
                                              int lg, R &acc, R &cmp) {
@@ -163,7 +171,7 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
                     const R F = fma(N, fd - fs, fma(fs, -fd, fd));
                     t = fma(b.w(j, k), F, t);
                 }
-                two_sum(acc, cmp, t);
+                lane_add(acc, cmp, t);
             }
         } else {  // F_abs = N(f-f') - f'(1-f)
             const R u = R(1) - fd;
@@ -178,7 +186,7 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
                     const R F = fma(N, fd - fs, -fs * u);
                     t = fma(b.w(j, k), F, t);
                 }
-                two_sum(acc, cmp, t);
+                lane_add(acc, cmp, t);
             }
         }
     } else if (V.part == PART_PHE) {  // F_abs(f_d, f_s, N_p) with N_p per item
@@ -195,7 +203,7 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
                 const R F = fma(Np, fd - fs, -fs * (R(1) - fd));
                 t = fma(b.w(j, k), F, t);
             }
-            two_sum(acc, cmp, t);
+            lane_add(acc, cmp, t);
         }
     } else {
         const unsigned pmask = (1u << V.pb) - 1u;
@@ -212,7 +220,7 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
                     const R G = fma(-Nb, Nc, fma(Na, Nb + Nc, Na));
                     t = fma(b.w(j, k), G, t);
                 }
-                two_sum(acc, cmp, t);
+                lane_add(acc, cmp, t);
             }
         } else {  // G_abs = N(N''-N') - N'(N''+1)
 #pragma unroll
@@ -226,7 +234,7 @@ __device__ __forceinline__ void compute_item(const GroupView<R> &V, const Item &
                     const R G = fma(Na, Nc - Nb, -Nb * (Nc + R(1)));
                     t = fma(b.w(j, k), G, t);
                 }
-                two_sum(acc, cmp, t);
+                lane_add(acc, cmp, t);
             }
         }
     }
